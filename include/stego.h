@@ -1,0 +1,271 @@
+/*
+ * stego.h -- C ABI of the GB300 LSB substitution steganography library
+ * (libstego.so, built for sm_103a).
+ *
+ * The method (Patel, Pradhan and Ambegaokar, "A Novel Approach for
+ * Implementing Steganography with Computing Power Obtained by Combining CUDA
+ * and MATLAB"): hide a message in the least significant bits of uint8 cover
+ * image or video-frame bytes (Section VI, embedding) and read it back
+ * (Section VII, extraction).  Two bit layouts are provided:
+ *
+ *   STEGO_LAYOUT_STREAM1  one bit per cover byte, over the cover bytes in
+ *       memory order (row-major, interleaved channels).  The embedded stream
+ *       is S = BE32(8*m) || msg with STEGO_HEADER_BE32 (a 32-bit big-endian
+ *       count of message bits, then the message), or S = msg without it.
+ *       Cover byte k carries bit k of S, bits taken most significant first
+ *       within each stream byte:
+ *           stego[k] = (cover[k] & 0xFE) | ((S[k/8] >> (7 - k%8)) & 1),
+ *       for k < T = 8*|S|; bytes k >= T are the cover's.  This is the
+ *       Section VI substitution rule (clear low bits, OR in message bits)
+ *       with one bit per byte and a sequential layout.
+ *
+ *   STEGO_LAYOUT_PAPER2   Sections VI and VII as printed: one colour plane
+ *       (Section VI step 2) of an H x W x channels interleaved image, two
+ *       bits per cover byte, the message divided greedily among rows with
+ *       L = min(remaining, floor(W/4)) bytes per row (Section VII step 4), and
+ *       bit pair i (bits 2i..2i+1) of data byte B[j] written to row position
+ *       A[L*i + j] (Section VI step 7):
+ *           A[L*i + j] = (A[L*i + j] & 0xFC) | ((B[j] >> 2i) & 3).
+ *       The length is passed out of band, as the paper's extract(E, N) call
+ *       does (Section VIII).
+ *
+ * Conventions common to every entry point
+ *   - Pointers named d_* are device pointers (CUDA global memory of the
+ *     current device).  Pointers to stego_geom / stego_tune are host
+ *     pointers, read before the call returns.  The caller owns every buffer;
+ *     the library allocates no device memory in any call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous and stream-ordered; none synchronises the device.
+ *   - Errors detectable from the arguments (null pointers, sizes, capacity,
+ *     geometry, flags, overlapping buffers) are returned synchronously and
+ *     nothing is launched or written.  Errors that depend on device data (a
+ *     malformed header, a message buffer too small for the header's length)
+ *     are written to the stego_result status field on the device; in that
+ *     case the message buffer is not written.  STEGO_E_CUDA means a CUDA
+ *     launch or memset failed (see cudaGetLastError in the caller's runtime).
+ *   - Any byte alignment is accepted.  Cover and stego buffers that start on
+ *     16-byte boundaries take the vectorised (128-bit) path.
+ *   - In-place embedding (d_stego == d_cover) is allowed and then bytes past
+ *     the embedded bits are not written.  Any other overlap between the
+ *     buffers of one call is STEGO_E_INVAL.
+ */
+#ifndef STEGO_H
+#define STEGO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Status codes                                                        */
+/* ------------------------------------------------------------------ */
+enum stego_status {
+    STEGO_OK = 0,
+    STEGO_E_INVAL = -1,         /* bad argument, flag, geometry or overlap    */
+    STEGO_E_CAPACITY = -2,      /* message does not fit in the cover          */
+    STEGO_E_BAD_HEADER = -3,    /* header absent, not whole bytes, too long   */
+    STEGO_E_MSG_TOO_SMALL = -4, /* output message buffer smaller than length  */
+    STEGO_E_CUDA = -5,          /* a CUDA runtime call failed                 */
+    STEGO_E_NOMEM = -6,         /* caller-supplied workspace too small        */
+    STEGO_E_TIMEOUT = -7        /* reserved for bounded device-side waits     */
+};
+
+/* ------------------------------------------------------------------ */
+/* Flags                                                               */
+/* ------------------------------------------------------------------ */
+#define STEGO_LAYOUT_STREAM1 0x0u
+#define STEGO_LAYOUT_PAPER2 0x1u
+#define STEGO_LAYOUT_MASK 0xFu
+#define STEGO_HEADER_BE32 0x10u /* STREAM1 only: 32-bit big-endian bit count */
+#define STEGO_FUSE_STATS 0x20u  /* embed: count changed bytes and SSE      */
+
+/* Image geometry for STEGO_LAYOUT_PAPER2: `height` rows of `width` pixels
+ * with `channels` interleaved uint8 channels; the message goes into channel
+ * `plane` (Section VI step 2).  cover_bytes must equal width*height*channels. */
+typedef struct stego_geom {
+    uint32_t width;
+    uint32_t height;
+    uint32_t channels;
+    uint32_t plane;
+} stego_geom;
+
+/* Per-call result, in device memory (32 bytes, 8-byte aligned).
+ *   changed    embed with STEGO_FUSE_STATS: number of bytes whose value
+ *              changed; otherwise 0.
+ *   sse        embed with STEGO_FUSE_STATS: sum over all cover bytes of
+ *              (stego - cover)^2 (exact, integer); MSE = sse / cover_bytes and
+ *              PSNR = 10 log10(255^2 / MSE), the Section VIII quality figure.
+ *   msg_bytes  embed: message bytes embedded; extract: bytes extracted.
+ *   status     STEGO_OK or the device-detected error of the call. */
+typedef struct stego_result {
+    uint64_t changed;
+    uint64_t sse;
+    uint64_t msg_bytes;
+    int32_t status;
+    int32_t reserved;
+} stego_result;
+
+/* One cover of a batched call (device memory, 72 bytes, 8-byte aligned).
+ *   cover        embed: the cover; extract: the stego image to read.
+ *   stego        embed: output image (may equal cover); extract: unused.
+ *   msg          embed: message to hide (read); extract: output buffer.
+ *   cover_bytes  size of cover (and stego) in bytes.
+ *   msg_bytes    embed: message length; extract: capacity of msg.
+ *   msg_len      extract without a header (raw STREAM1, PAPER2): bytes to
+ *                extract; ignored otherwise.
+ *   flags        layout and header flags as for the single calls
+ *                (STEGO_FUSE_STATS is taken from the batched call instead).
+ *   geom         PAPER2 geometry. */
+typedef struct stego_desc {
+    const uint8_t *cover;
+    uint8_t *stego;
+    uint8_t *msg;
+    uint64_t cover_bytes;
+    uint64_t msg_bytes;
+    uint64_t msg_len;
+    uint32_t flags;
+    uint32_t reserved;
+    stego_geom geom;
+} stego_desc;
+
+/* Launch shape.  Zero fields take the library's current choice for the
+ * operation (installed by stego_set_tune, initially built-in defaults).
+ *   threads         threads per CTA (multiple of 32, 64..512)
+ *   vec_per_thread  16-byte vectors each thread keeps in flight per loop
+ *                   iteration (1, 2, 4 or 8)
+ *   ctas_per_sm     resident CTAs per SM of the persistent grid
+ *   tile_bytes      batched calls: cover bytes per work tile (a multiple of
+ *                   4096, at least 4096) */
+typedef struct stego_tune {
+    uint32_t threads;
+    uint32_t vec_per_thread;
+    uint32_t ctas_per_sm;
+    uint32_t tile_bytes;
+} stego_tune;
+
+enum stego_op {
+    STEGO_OP_EMBED = 0,
+    STEGO_OP_EXTRACT = 1,
+    STEGO_OP_CHANGED = 2,
+    STEGO_OP_EMBED_BATCHED = 3,
+    STEGO_OP_EXTRACT_BATCHED = 4,
+    STEGO_OP_COUNT = 5
+};
+
+/* Library version (major*10000 + minor*100 + patch). */
+int stego_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *stego_strerror(int status);
+
+/* Largest message (bytes) that fits a cover of `cover_bytes`:
+ *   STREAM1 with header: floor(C/8) - 4 (at least 0, at most 2^29 - 1;
+ *                        a cover under 32 bytes cannot hold the header, so
+ *                        even an empty message is STEGO_E_CAPACITY there);
+ *   STREAM1 raw:        floor(C/8);
+ *   PAPER2:             floor(W/4) * H   (Section VI step 5: 4*|B| <= |A|).
+ * geom is required for PAPER2 and ignored otherwise.  Writes *out_msg_bytes.
+ * Returns STEGO_OK or STEGO_E_INVAL. */
+int stego_capacity(uint64_t cover_bytes, const stego_geom *geom, uint32_t flags,
+                   uint64_t *out_msg_bytes);
+
+/* Embed (Section VI).  Writes cover_bytes bytes of d_stego (out of place) or
+ * the T = 8*|S| carrying bytes (STREAM1 in place) / the 4*msg_bytes plane
+ * bytes (PAPER2 in place).
+ *   d_cover, d_stego  cover and output image, cover_bytes each.
+ *   d_msg, msg_bytes  message (may be NULL when msg_bytes == 0).
+ *   geom              PAPER2 geometry (host pointer) or NULL for STREAM1.
+ *   flags             layout | STEGO_HEADER_BE32 (STREAM1) | STEGO_FUSE_STATS.
+ *   d_result          optional; required with STEGO_FUSE_STATS.  Filled with
+ *                     changed/sse (if fused), msg_bytes and status STEGO_OK.
+ * Synchronous errors: STEGO_E_INVAL, STEGO_E_CAPACITY (message too long for
+ * the cover; nothing written), STEGO_E_CUDA. */
+int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
+                const uint8_t *d_msg, uint64_t msg_bytes, const stego_geom *geom,
+                uint32_t flags, stego_result *d_result, void *stream);
+
+/* Extract (Section VII).
+ *   d_stego, cover_bytes  the stego image.
+ *   d_msg, msg_cap        output buffer and its capacity in bytes.
+ *   msg_len               bytes to extract without a header (raw STREAM1 and
+ *                         PAPER2, the paper's out-of-band N); ignored with
+ *                         STEGO_HEADER_BE32.
+ *   d_result              required with STEGO_HEADER_BE32 (the length and
+ *                         status come from the device); optional otherwise.
+ * With the header, the 32-bit count is read from the LSBs of bytes 0..31 and
+ * is rejected on the device (status STEGO_E_BAD_HEADER) when the stego is
+ * shorter than 32 bytes, the count is not a multiple of 8 or 32 + count
+ * exceeds cover_bytes; STEGO_E_MSG_TOO_SMALL when count/8 > msg_cap.  On any
+ * device-side error d_msg is not written and msg_bytes is 0.
+ * Without the header the bounds are checked on the host: STEGO_E_CAPACITY
+ * when msg_len exceeds stego_capacity, STEGO_E_MSG_TOO_SMALL when
+ * msg_len > msg_cap. */
+int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
+                  uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom,
+                  uint32_t flags, stego_result *d_result, void *stream);
+
+/* Changed-byte count and squared error of two equal-length byte arrays
+ * (Section VIII reports PSNR of stego against cover).
+ *   d_out2[0] = #{k : a[k] != b[k]},  d_out2[1] = sum (a[k] - b[k])^2.
+ * d_out2 is device memory, two uint64 (8-byte aligned). */
+int stego_changed_bytes(const uint8_t *d_a, const uint8_t *d_b, uint64_t n,
+                        uint64_t *d_out2, void *stream);
+
+/* Device workspace (bytes) a batched call over n descriptors needs. */
+uint64_t stego_batched_workspace_bytes(uint32_t n);
+
+/* Batched embed: every descriptor of d_descs[0..n) (device memory) in one
+ * persistent launch that claims fixed-size tiles of the covers from a work
+ * counter.  The paper repeats the per-row routine over rows and video frames
+ * (Section VI, last paragraph; "image/video frames", Section III); here all
+ * covers and frames of a batch are one launch.
+ *   d_results  n results (device), one per descriptor: status, msg_bytes and,
+ *              with STEGO_FUSE_STATS in `flags`, changed and sse.
+ *   flags      STEGO_FUSE_STATS or 0 (per-cover layout flags are in the
+ *              descriptors).
+ *   tune       optional launch shape (host pointer); NULL = current choice.
+ *   d_ws       caller-owned device workspace of ws_bytes >=
+ *              stego_batched_workspace_bytes(n), 16-byte aligned.  It is
+ *              scratch: its contents on entry do not matter and on return
+ *              are unspecified.
+ * Descriptor errors (capacity, geometry, overlap) are per cover: that
+ * cover's status is set and its output is not written; other covers
+ * proceed.  Returns STEGO_E_NOMEM when ws_bytes is too small. */
+int stego_embed_batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results,
+                        uint32_t flags, const stego_tune *tune, void *d_ws,
+                        uint64_t ws_bytes, void *stream);
+
+/* Batched extract (Section VII); same arguments.  Each descriptor's cover is
+ * the stego image and msg its output buffer of msg_bytes capacity. */
+int stego_extract_batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results,
+                          uint32_t flags, const stego_tune *tune, void *d_ws,
+                          uint64_t ws_bytes, void *stream);
+
+/* CUDA graph of one batched call.  The descriptors, results and workspace
+ * are captured by address: fill the same device arrays with new descriptors
+ * (same n) and replay, which re-runs the three launches of the call without
+ * host-side launch overhead.  The graph object (and its instantiation) is
+ * the only thing these functions create; stego_graph_destroy releases it.
+ *   op  STEGO_OP_EMBED_BATCHED or STEGO_OP_EXTRACT_BATCHED.
+ * Capture uses a private stream in thread-local capture mode, so it does not
+ * disturb work the caller has in flight. */
+typedef struct stego_graph stego_graph;
+int stego_graph_capture_batched(int op, const stego_desc *d_descs, uint32_t n,
+                                stego_result *d_results, uint32_t flags, const stego_tune *tune,
+                                void *d_ws, uint64_t ws_bytes, stego_graph **out);
+int stego_graph_launch(stego_graph *g, void *stream);
+int stego_graph_destroy(stego_graph *g);
+
+/* Install / read the launch shape used by an operation (enum stego_op) on
+ * every device.  Zero fields of `t` keep their built-in defaults.
+ * Returns STEGO_E_INVAL for an unknown op or an out-of-range field. */
+int stego_set_tune(int op, const stego_tune *t);
+int stego_get_tune(int op, stego_tune *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEGO_H */

@@ -1,2 +1,322 @@
-"""GB300-native LSB substitution steganography (embed / extract / changed
-bytes) behind a C-ABI CUDA library; see ``include/stego.h``."""
+"""GB300-native LSB substitution steganography.
+
+A thin Python binding over ``libstego.so`` (declared in ``include/stego.h``).
+Every function here only marshals torch tensors into device pointers and
+calls the C entry point of the same name; all steganography arithmetic runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams.
+
+There is no CPU fallback: if the library has not been built (see
+``paper_0912_0947_gb300.build.build()``) or a tensor is not a contiguous
+CUDA uint8 tensor, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+# -- flags / status (values of include/stego.h) ------------------------------
+LAYOUT_STREAM1 = 0x0
+LAYOUT_PAPER2 = 0x1
+HEADER_BE32 = 0x10
+FUSE_STATS = 0x20
+
+OK = 0
+E_INVAL = -1
+E_CAPACITY = -2
+E_BAD_HEADER = -3
+E_MSG_TOO_SMALL = -4
+E_CUDA = -5
+E_NOMEM = -6
+E_TIMEOUT = -7
+
+OP_EMBED, OP_EXTRACT, OP_CHANGED, OP_EMBED_BATCHED, OP_EXTRACT_BATCHED = range(5)
+
+RESULT_WORDS = 4  # stego_result: changed, sse, msg_bytes, status|reserved (int64 view)
+
+# stego_desc as laid out in device memory (72 bytes)
+DESC_DTYPE = np.dtype([
+    ("cover", "<u8"), ("stego", "<u8"), ("msg", "<u8"),
+    ("cover_bytes", "<u8"), ("msg_bytes", "<u8"), ("msg_len", "<u8"),
+    ("flags", "<u4"), ("reserved", "<u4"),
+    ("width", "<u4"), ("height", "<u4"), ("channels", "<u4"), ("plane", "<u4"),
+])
+assert DESC_DTYPE.itemsize == 72
+
+
+class StegoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, strerror(status), status))
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("channels", ctypes.c_uint32), ("plane", ctypes.c_uint32)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("vec_per_thread", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("tile_bytes", ctypes.c_uint32)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_int = ctypes.c_int
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded ``libstego.so``; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libstego.so is not built (%s); run "
+                               "paper_0912_0947_gb300.build.build() first" % path)
+        L = ctypes.CDLL(path)
+        L.stego_version.restype = _int
+        L.stego_strerror.argtypes = [_int]
+        L.stego_strerror.restype = ctypes.c_char_p
+        L.stego_capacity.argtypes = [_u64, ctypes.POINTER(Geom), _u32, ctypes.POINTER(_u64)]
+        L.stego_capacity.restype = _int
+        L.stego_embed.argtypes = [_vp, _vp, _u64, _vp, _u64, ctypes.POINTER(Geom), _u32, _vp, _vp]
+        L.stego_embed.restype = _int
+        L.stego_extract.argtypes = [_vp, _u64, _vp, _u64, _u64, ctypes.POINTER(Geom), _u32, _vp, _vp]
+        L.stego_extract.restype = _int
+        L.stego_changed_bytes.argtypes = [_vp, _vp, _u64, _vp, _vp]
+        L.stego_changed_bytes.restype = _int
+        L.stego_batched_workspace_bytes.argtypes = [_u32]
+        L.stego_batched_workspace_bytes.restype = _u64
+        for name in ("stego_embed_batched", "stego_extract_batched"):
+            f = getattr(L, name)
+            f.argtypes = [_vp, _u32, _vp, _u32, ctypes.POINTER(Tune), _vp, _u64, _vp]
+            f.restype = _int
+        L.stego_set_tune.argtypes = [_int, ctypes.POINTER(Tune)]
+        L.stego_set_tune.restype = _int
+        L.stego_get_tune.argtypes = [_int, ctypes.POINTER(Tune)]
+        L.stego_get_tune.restype = _int
+        L.stego_graph_capture_batched.argtypes = [_int, _vp, _u32, _vp, _u32, ctypes.POINTER(Tune),
+                                                  _vp, _u64, ctypes.POINTER(_vp)]
+        L.stego_graph_capture_batched.restype = _int
+        L.stego_graph_launch.argtypes = [_vp, _vp]
+        L.stego_graph_launch.restype = _int
+        L.stego_graph_destroy.argtypes = [_vp]
+        L.stego_graph_destroy.restype = _int
+        _LIB = L
+    return _LIB
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().stego_strerror(int(status)).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _check(st: int, where: str) -> int:
+    if st != OK:
+        raise StegoError(st, where)
+    return st
+
+
+# -- marshalling helpers -------------------------------------------------------
+
+def _dev_ptr(t, what: str, dtype=torch.uint8):
+    """Device address of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % what)
+    if t.device.type != "cuda":
+        raise ValueError("%s must live on a CUDA device (no CPU fallback)" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream_ptr(stream, device=None):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _geom(geom):
+    if geom is None:
+        return None
+    if isinstance(geom, Geom):
+        return ctypes.byref(geom)
+    w, h, c, p = geom
+    return ctypes.byref(Geom(int(w), int(h), int(c), int(p)))
+
+
+def _tune(tune):
+    if tune is None:
+        return None
+    if isinstance(tune, Tune):
+        return ctypes.byref(tune)
+    return ctypes.byref(Tune(*[int(x) for x in tune]))
+
+
+def new_result(device="cuda", n: int | None = None) -> torch.Tensor:
+    """Device storage for one stego_result (n=None) or n of them (int64 view)."""
+    shape = (RESULT_WORDS,) if n is None else (n, RESULT_WORDS)
+    return torch.zeros(shape, dtype=torch.int64, device=device)
+
+
+def read_result(res: torch.Tensor) -> dict | list[dict]:
+    """Host view of stego_result(s): changed, sse, msg_bytes, status."""
+    a = res.detach().cpu().numpy()
+    one = a.ndim == 1
+    a = a.reshape(-1, RESULT_WORDS)
+    out = []
+    for row in a:
+        st = int(np.int64(row[3]).astype(np.uint64) & np.uint64(0xFFFFFFFF))
+        st = st - (1 << 32) if st >= (1 << 31) else st
+        out.append({"changed": int(row[0]), "sse": int(row[1]),
+                    "msg_bytes": int(row[2]), "status": st})
+    return out[0] if one else out
+
+
+# -- entry points (same names as the C ABI) ------------------------------------
+
+def stego_version() -> int:
+    return lib().stego_version()
+
+
+def stego_capacity(cover_bytes: int, flags: int, geom=None) -> int:
+    out = _u64(0)
+    _check(lib().stego_capacity(int(cover_bytes), _geom(geom), int(flags), ctypes.byref(out)),
+           "stego_capacity")
+    return int(out.value)
+
+
+def stego_embed(cover, stego, msg, flags: int, result=None, geom=None, stream=None) -> None:
+    """stego <- embed(cover, msg).  ``stego`` may be ``cover`` (in place)."""
+    c = _dev_ptr(cover, "cover")
+    s = _dev_ptr(stego, "stego")
+    m = _dev_ptr(msg, "msg") if msg is not None else None
+    r = _dev_ptr(result, "result", torch.int64)
+    if stego.numel() != cover.numel():
+        raise ValueError("cover and stego sizes differ")
+    st = lib().stego_embed(c, s, cover.numel(), m, 0 if msg is None else msg.numel(),
+                           _geom(geom), int(flags), r, _stream_ptr(stream, cover.device))
+    _check(st, "stego_embed")
+
+
+def stego_extract(stego, msg, msg_len: int, flags: int, result=None, geom=None,
+                  stream=None) -> None:
+    """msg <- extract(stego).  With HEADER_BE32 the length (and status) go to
+    ``result``; otherwise ``msg_len`` bytes are extracted."""
+    s = _dev_ptr(stego, "stego")
+    m = _dev_ptr(msg, "msg") if msg is not None else None
+    r = _dev_ptr(result, "result", torch.int64)
+    st = lib().stego_extract(s, stego.numel(), m, 0 if msg is None else msg.numel(),
+                             int(msg_len), _geom(geom), int(flags), r,
+                             _stream_ptr(stream, stego.device))
+    _check(st, "stego_extract")
+
+
+def stego_changed_bytes(a, b, out2, stream=None) -> None:
+    """out2 (int64[2], device) <- [changed bytes, sum of squared differences]."""
+    if a.numel() != b.numel():
+        raise ValueError("sizes differ")
+    st = lib().stego_changed_bytes(_dev_ptr(a, "a"), _dev_ptr(b, "b"), a.numel(),
+                                   _dev_ptr(out2, "out2", torch.int64),
+                                   _stream_ptr(stream, a.device))
+    _check(st, "stego_changed_bytes")
+
+
+def stego_batched_workspace_bytes(n: int) -> int:
+    return int(lib().stego_batched_workspace_bytes(int(n)))
+
+
+def stego_embed_batched(descs, n: int, results, flags: int, ws, tune=None, stream=None) -> None:
+    st = lib().stego_embed_batched(_dev_ptr(descs, "descs", None), int(n),
+                                   _dev_ptr(results, "results", torch.int64), int(flags),
+                                   _tune(tune), _dev_ptr(ws, "ws", None),
+                                   ws.numel() * ws.element_size(),
+                                   _stream_ptr(stream, descs.device))
+    _check(st, "stego_embed_batched")
+
+
+def stego_extract_batched(descs, n: int, results, flags: int, ws, tune=None, stream=None) -> None:
+    st = lib().stego_extract_batched(_dev_ptr(descs, "descs", None), int(n),
+                                     _dev_ptr(results, "results", torch.int64), int(flags),
+                                     _tune(tune), _dev_ptr(ws, "ws", None),
+                                     ws.numel() * ws.element_size(),
+                                     _stream_ptr(stream, descs.device))
+    _check(st, "stego_extract_batched")
+
+
+def stego_set_tune(op: int, tune) -> None:
+    t = tune if isinstance(tune, Tune) else Tune(*[int(x) for x in tune])
+    _check(lib().stego_set_tune(int(op), ctypes.byref(t)), "stego_set_tune")
+
+
+def stego_get_tune(op: int) -> Tune:
+    t = Tune()
+    _check(lib().stego_get_tune(int(op), ctypes.byref(t)), "stego_get_tune")
+    return t
+
+
+class BatchedGraph:
+    """A captured batched call (stego_graph_capture_batched); replay with
+    ``launch(stream)``."""
+
+    def __init__(self, op: int, descs, n: int, results, flags: int, ws, tune=None):
+        h = _vp(0)
+        st = lib().stego_graph_capture_batched(int(op), _dev_ptr(descs, "descs", None), int(n),
+                                               _dev_ptr(results, "results", torch.int64),
+                                               int(flags), _tune(tune), _dev_ptr(ws, "ws", None),
+                                               ws.numel() * ws.element_size(), ctypes.byref(h))
+        _check(st, "stego_graph_capture_batched")
+        self._h = h
+        # keep the captured buffers alive as long as the graph
+        self._keep = (descs, results, ws)
+
+    def launch(self, stream=None) -> None:
+        _check(lib().stego_graph_launch(self._h, _stream_ptr(stream)), "stego_graph_launch")
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            lib().stego_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# -- descriptor packing (host side) ---------------------------------------------
+
+def pack_descs(items) -> np.ndarray:
+    """Pack a list of dicts (keys of DESC_DTYPE; tensors allowed for cover,
+    stego, msg) into a host array of stego_desc records."""
+    a = np.zeros(len(items), dtype=DESC_DTYPE)
+    for i, it in enumerate(items):
+        for k, v in it.items():
+            if isinstance(v, torch.Tensor):
+                v = _dev_ptr(v, k) or 0
+            a[i][k] = v
+    return a
+
+
+def descs_to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
+    t = torch.from_numpy(a.view(np.uint8).copy())
+    return t.to(device)

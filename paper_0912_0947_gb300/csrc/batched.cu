@@ -1,0 +1,523 @@
+// batched.cu -- many covers or video frames of uneven sizes in one persistent
+// launch.  The paper runs its routine once per image row and per frame
+// (Section VI, last paragraph; image/video frames, Section III) with a
+// device allocation, two copies and a launch each time; here every cover of
+// a batch is cut into fixed-size tiles that one persistent grid claims from
+// a work counter.
+//
+// Per call, three stream-ordered launches (all capturable in a CUDA graph):
+//   1. prep      one thread per descriptor: validate it, (extract) read its
+//                32-bit header, write its result and its tile count;
+//   2. scan      one CTA: exclusive scan of the tile counts into tile
+//                offsets, total, work counter reset;
+//   3. persist   SMs x occupancy CTAs: claim `chunk` consecutive tiles at a
+//                time with one atomicAdd (the next claim is issued while the
+//                current chunk is processed), find the owning descriptor by
+//                binary search over the offsets once per chunk, and run the
+//                same per-vector code as the single-cover kernels on each
+//                tile.
+// Workspace (caller-owned scratch, 16-byte aligned):
+//   [0, 64)                 head: total tiles, work counter
+//   [64, 64 + 8(n+1))       tile offsets (counts before the scan)
+//   [info_off, +32n)        per-descriptor derived sizes and flags
+#include <cstring>
+
+#include "s1_device.cuh"
+
+namespace stego {
+namespace {
+
+struct WsHead {
+    unsigned long long total;
+    unsigned long long counter;
+    unsigned long long pad[6];
+};
+
+struct DescInfo {
+    uint64_t n_bytes; // embed: bytes written; extract: carrying bytes 8*len
+    uint64_t t_bytes; // embed: carrying bytes
+    uint64_t len;     // embed: stream bytes; extract: message bytes
+    uint32_t nbits;   // header value
+    uint32_t bits;    // kHeader | kVec | kMsgEven
+};
+
+constexpr uint32_t kHeader = 1u, kVec = 2u, kMsgEven = 4u;
+constexpr uint32_t kChunk = 4u; // tiles per claim
+
+uint64_t info_off(uint32_t n) { return (64ull + 8ull * ((uint64_t)n + 1) + 15ull) & ~15ull; }
+
+struct WsView {
+    WsHead *head;
+    unsigned long long *start;
+    DescInfo *info;
+};
+
+WsView ws_view(void *ws, uint32_t n)
+{
+    WsView v;
+    v.head = reinterpret_cast<WsHead *>(ws);
+    v.start = reinterpret_cast<unsigned long long *>((char *)ws + 64);
+    v.info = reinterpret_cast<DescInfo *>((char *)ws + info_off(n));
+    return v;
+}
+
+__device__ __forceinline__ bool d_overlap(const void *p, uint64_t np, const void *q, uint64_t nq)
+{
+    if (np == 0 || nq == 0 || p == nullptr || q == nullptr)
+        return false;
+    const uintptr_t a = (uintptr_t)p, b = (uintptr_t)q;
+    return a < b + nq && b < a + np;
+}
+
+__device__ __forceinline__ bool d_aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---------------------------------------------------------------------------
+// 1. prep
+// ---------------------------------------------------------------------------
+
+__global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *results, WsView ws,
+                           uint32_t tile_bytes)
+{
+    for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+        const stego_desc D = descs[d];
+        const uint32_t layout = D.flags & STEGO_LAYOUT_MASK;
+        const bool header = (D.flags & STEGO_HEADER_BE32) != 0;
+        const bool inplace = D.stego == D.cover;
+        int st = STEGO_OK;
+        if (D.flags & ~(STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS))
+            st = STEGO_E_INVAL;
+        else if (layout != STEGO_LAYOUT_STREAM1)
+            st = STEGO_E_INVAL; // the batched path carries the one-bit stream layout
+        else if (D.cover_bytes > 0 && (!D.cover || !D.stego))
+            st = STEGO_E_INVAL;
+        else if (D.msg_bytes > 0 && !D.msg)
+            st = STEGO_E_INVAL;
+        else if (!inplace && d_overlap(D.cover, D.cover_bytes, D.stego, D.cover_bytes))
+            st = STEGO_E_INVAL;
+        else if (d_overlap(D.msg, D.msg_bytes, D.stego, D.cover_bytes))
+            st = STEGO_E_INVAL;
+        else {
+            uint64_t cap = D.cover_bytes / 8u;
+            if (header) {
+                cap = cap >= 4u ? cap - 4u : 0u;
+                if (cap > 0x1FFFFFFFull)
+                    cap = 0x1FFFFFFFull;
+            }
+            if (D.msg_bytes > cap || (header && D.cover_bytes < 32))
+                st = STEGO_E_CAPACITY;
+        }
+        DescInfo inf;
+        inf.n_bytes = inf.t_bytes = inf.len = 0;
+        inf.nbits = 0;
+        inf.bits = 0;
+        unsigned long long tiles = 0;
+        if (st == STEGO_OK) {
+            inf.len = D.msg_bytes + (header ? 4u : 0u);
+            inf.t_bytes = 8u * inf.len;
+            inf.n_bytes = inplace ? inf.t_bytes : D.cover_bytes;
+            inf.nbits = (uint32_t)(8u * D.msg_bytes);
+            inf.bits = (header ? kHeader : 0u) |
+                       ((d_aligned16(D.cover) && d_aligned16(D.stego)) ? kVec : 0u) |
+                       ((((uintptr_t)D.msg & 1u) == 0) ? kMsgEven : 0u);
+            tiles = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
+        }
+        ws.info[d] = inf;
+        ws.start[d] = tiles;
+        stego_result r;
+        r.changed = 0;
+        r.sse = 0;
+        r.msg_bytes = st == STEGO_OK ? D.msg_bytes : 0u;
+        r.status = st;
+        r.reserved = 0;
+        results[d] = r;
+    }
+}
+
+__global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *results,
+                             WsView ws, uint32_t tile_bytes)
+{
+    for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+        const stego_desc D = descs[d];
+        const uint32_t layout = D.flags & STEGO_LAYOUT_MASK;
+        const bool header = (D.flags & STEGO_HEADER_BE32) != 0;
+        int st = STEGO_OK;
+        uint64_t len = 0;
+        uint32_t nbits = 0;
+        if (D.flags & ~(STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS))
+            st = STEGO_E_INVAL;
+        else if (layout != STEGO_LAYOUT_STREAM1)
+            st = STEGO_E_INVAL;
+        else if (D.cover_bytes > 0 && !D.cover)
+            st = STEGO_E_INVAL;
+        else if (D.msg_bytes > 0 && !D.msg)
+            st = STEGO_E_INVAL;
+        else if (d_overlap(D.msg, D.msg_bytes, D.cover, D.cover_bytes))
+            st = STEGO_E_INVAL;
+        else if (header) {
+            if (D.cover_bytes < 32) {
+                st = STEGO_E_BAD_HEADER;
+            } else {
+                for (int k = 0; k < 32; ++k)
+                    nbits |= (uint32_t)(D.cover[k] & 1u) << (31 - k);
+                st = s1::header_status(D.cover_bytes, D.msg_bytes, nbits);
+                len = nbits >> 3;
+            }
+        } else {
+            len = D.msg_len;
+            if (len > D.cover_bytes / 8u)
+                st = STEGO_E_CAPACITY;
+            else if (len > D.msg_bytes)
+                st = STEGO_E_MSG_TOO_SMALL;
+        }
+        if (st != STEGO_OK)
+            len = 0;
+        DescInfo inf;
+        inf.len = len;
+        inf.n_bytes = 8u * len;
+        inf.t_bytes = 0;
+        inf.nbits = nbits;
+        inf.bits = (header ? kHeader : 0u) | (d_aligned16(D.cover) ? kVec : 0u) |
+                   ((((uintptr_t)D.msg & 1u) == 0) ? kMsgEven : 0u);
+        ws.info[d] = inf;
+        ws.start[d] = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
+        stego_result r;
+        r.changed = 0;
+        r.sse = 0;
+        r.msg_bytes = len;
+        r.status = st;
+        r.reserved = 0;
+        results[d] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. scan (one CTA of kScanThreads)
+// ---------------------------------------------------------------------------
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles(WsView ws, uint32_t n)
+{
+    __shared__ unsigned long long part[kScanThreads];
+    const uint32_t t = threadIdx.x, T = blockDim.x;
+    const uint64_t seg = ((uint64_t)n + T - 1) / T;
+    const uint64_t b = (uint64_t)t * seg;
+    const uint64_t e = b + seg < n ? b + seg : n;
+    unsigned long long sum = 0;
+    for (uint64_t i = b; i < e; ++i)
+        sum += ws.start[i];
+    part[t] = sum;
+    __syncthreads();
+    for (uint32_t off = 1; off < T; off <<= 1) {
+        const unsigned long long v = t >= off ? part[t - off] : 0ull;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[t] - sum;
+    for (uint64_t i = b; i < e; ++i) {
+        const unsigned long long c = ws.start[i];
+        ws.start[i] = run;
+        run += c;
+    }
+    if (t == T - 1) {
+        ws.start[n] = part[T - 1];
+        ws.head->total = part[T - 1];
+        ws.head->counter = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. persistent kernels
+// ---------------------------------------------------------------------------
+
+// Largest d < n with start[d] <= t (start[0] = 0 <= t < start[n]).
+__device__ __forceinline__ uint32_t owner_of(const unsigned long long *start, uint32_t n,
+                                             unsigned long long t)
+{
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (start[mid] <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Warp-level flush of per-thread statistics into one descriptor's result.
+__device__ __forceinline__ void flush_stats(unsigned long long &changed, unsigned long long &sse,
+                                            stego_result *res)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        changed += __shfl_down_sync(0xFFFFFFFFu, changed, o);
+        sse += __shfl_down_sync(0xFFFFFFFFu, sse, o);
+    }
+    if ((threadIdx.x & 31u) == 0 && res) {
+        if (changed)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&res->changed), changed);
+        if (sse)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&res->sse), sse);
+    }
+    changed = 0;
+    sse = 0;
+}
+
+// The claim loop shared by both directions: calls body(d, local_tile) for
+// every tile this CTA claims, in order.
+template <typename Body>
+__device__ __forceinline__ void claim_loop(const WsView &ws, uint32_t n, Body &&body)
+{
+    __shared__ unsigned long long s_claim;
+    const unsigned long long total = ws.head->total;
+    if (threadIdx.x == 0)
+        s_claim = atomicAdd(&ws.head->counter, (unsigned long long)kChunk);
+    __syncthreads();
+    for (;;) {
+        const unsigned long long c0 = s_claim;
+        __syncthreads(); // every thread has read the claim
+        if (c0 >= total)
+            break;
+        if (threadIdx.x == 0) // next claim in flight while this chunk runs
+            s_claim = atomicAdd(&ws.head->counter, (unsigned long long)kChunk);
+        const unsigned long long c1 = c0 + kChunk < total ? c0 + kChunk : total;
+        uint32_t d = owner_of(ws.start, n, c0);
+        for (unsigned long long t = c0; t < c1; ++t) {
+            while (ws.start[d + 1] <= t)
+                ++d;
+            body(d, t - ws.start[d]);
+        }
+        __syncthreads(); // the next claim is visible
+    }
+}
+
+template <int V, bool STATS>
+__global__ void __launch_bounds__(512) persist_embed(const stego_desc *descs, uint32_t n,
+                                                     stego_result *results, WsView ws,
+                                                     uint32_t tile_bytes)
+{
+    unsigned long long changed = 0, sse = 0;
+    uint32_t stat_d = 0xFFFFFFFFu;
+    claim_loop(ws, n, [&](uint32_t d, unsigned long long lt) {
+        if (STATS && d != stat_d) {
+            flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+            stat_d = d;
+        }
+        const stego_desc &D = descs[d];
+        const DescInfo inf = ws.info[d];
+        s1::EmbedView a;
+        a.cover = D.cover;
+        a.stego = D.stego;
+        a.msg = D.msg;
+        a.n_bytes = inf.n_bytes;
+        a.t_bytes = inf.t_bytes;
+        a.slen = inf.len;
+        a.header = (inf.bits & kHeader) ? 1u : 0u;
+        a.nbits = inf.nbits;
+        a.msg_even = (inf.bits & kMsgEven) ? 1u : 0u;
+        a.pad = 0;
+        const uint64_t b0 = lt * tile_bytes;
+        const uint64_t b1 = b0 + tile_bytes < inf.n_bytes ? b0 + tile_bytes : inf.n_bytes;
+        if (inf.bits & kVec) {
+            s1::embed_vec_range<V, STATS>(a, (b0 >> 4) + threadIdx.x, b1 >> 4,
+                                          (uint64_t)blockDim.x * V, changed, sse);
+            if (b1 == inf.n_bytes)
+                s1::embed_tail<STATS>(a, changed, sse);
+        } else {
+            s1::embed_bytes_range<STATS>(a, (b0 >> 3) + threadIdx.x, (b1 + 7) >> 3, blockDim.x,
+                                         changed, sse);
+        }
+    });
+    if (STATS)
+        flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+}
+
+template <int V>
+__global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, uint32_t n,
+                                                       WsView ws, uint32_t tile_bytes)
+{
+    claim_loop(ws, n, [&](uint32_t d, unsigned long long lt) {
+        const stego_desc &D = descs[d];
+        const DescInfo inf = ws.info[d];
+        s1::ExtractView x;
+        x.st = D.cover;
+        x.msg = D.msg;
+        x.len = inf.len;
+        x.base = (inf.bits & kHeader) ? 32u : 0u;
+        x.msg_even = (inf.bits & kMsgEven) ? 1u : 0u;
+        x.pad = 0;
+        const uint64_t b0 = lt * tile_bytes;
+        const uint64_t b1 = b0 + tile_bytes < inf.n_bytes ? b0 + tile_bytes : inf.n_bytes;
+        if (inf.bits & kVec) {
+            s1::extract_vec_range<V>(x, (b0 >> 4) + threadIdx.x, b1 >> 4, (uint64_t)blockDim.x * V);
+            if (b1 == inf.n_bytes && (x.len & 1u) && threadIdx.x == 0)
+                s1::extract_one(x, x.len - 1);
+        } else {
+            s1::extract_bytes_range(x, (b0 >> 3) + threadIdx.x, b1 >> 3, blockDim.x);
+        }
+    });
+}
+
+template <bool EMBED>
+const void *persist_kernel(int vec, bool stats)
+{
+    if (EMBED) {
+        switch (vec) {
+        case 1: return stats ? (const void *)persist_embed<1, true> : (const void *)persist_embed<1, false>;
+        case 2: return stats ? (const void *)persist_embed<2, true> : (const void *)persist_embed<2, false>;
+        case 8: return stats ? (const void *)persist_embed<8, true> : (const void *)persist_embed<8, false>;
+        default: return stats ? (const void *)persist_embed<4, true> : (const void *)persist_embed<4, false>;
+        }
+    }
+    switch (vec) {
+    case 1: return (const void *)persist_extract<1>;
+    case 2: return (const void *)persist_extract<2>;
+    case 8: return (const void *)persist_extract<8>;
+    default: return (const void *)persist_extract<4>;
+    }
+}
+
+uint64_t workspace_bytes(uint32_t n) { return info_off(n) + sizeof(DescInfo) * (uint64_t)n; }
+
+template <bool EMBED>
+int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint32_t flags,
+            const stego_tune *tune, void *d_ws, uint64_t ws_bytes, void *stream)
+{
+    if (flags & ~(uint32_t)STEGO_FUSE_STATS)
+        return STEGO_E_INVAL;
+    if (!EMBED && (flags & STEGO_FUSE_STATS))
+        return STEGO_E_INVAL;
+    if (tune && !tune_ok(tune))
+        return STEGO_E_INVAL;
+    if (n == 0)
+        return STEGO_OK;
+    if (!d_descs || !d_results || !d_ws)
+        return STEGO_E_INVAL;
+    if (((uintptr_t)d_descs & 7u) || ((uintptr_t)d_results & 7u) || ((uintptr_t)d_ws & 15u))
+        return STEGO_E_INVAL;
+    if (ws_bytes < workspace_bytes(n))
+        return STEGO_E_NOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Shape sh = shape_for(EMBED ? STEGO_OP_EMBED_BATCHED : STEGO_OP_EXTRACT_BATCHED, tune);
+    const uint32_t tile = sh.tile_bytes;
+    WsView ws = ws_view(d_ws, n);
+
+    const int prep_threads = 256;
+    int prep_grid = (int)((n + prep_threads - 1) / prep_threads);
+    const int prep_cap = sm_count() * 8;
+    if (prep_grid > prep_cap)
+        prep_grid = prep_cap;
+    if (EMBED)
+        prep_embed<<<prep_grid, prep_threads, 0, s>>>(d_descs, n, d_results, ws, tile);
+    else
+        prep_extract<<<prep_grid, prep_threads, 0, s>>>(d_descs, n, d_results, ws, tile);
+    if (cudaGetLastError() != cudaSuccess)
+        return STEGO_E_CUDA;
+    scan_tiles<<<1, kScanThreads, 0, s>>>(ws, n);
+    if (cudaGetLastError() != cudaSuccess)
+        return STEGO_E_CUDA;
+
+    const bool stats = (flags & STEGO_FUSE_STATS) != 0;
+    const void *k = persist_kernel<EMBED>(sh.vec, stats);
+    // the tile count lives on the device: launch the full persistent grid
+    const int grid = persistent_grid(k, sh.threads, 0, sh.ctas_per_sm, ~0ull >> 1, 1);
+    cudaError_t e;
+    if (EMBED) {
+        void *args[] = {(void *)&d_descs, &n, &d_results, &ws, (void *)&tile};
+        e = cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+    } else {
+        void *args[] = {(void *)&d_descs, &n, &ws, (void *)&tile};
+        e = cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+    }
+    return e == cudaSuccess ? STEGO_OK : STEGO_E_CUDA;
+}
+
+} // namespace
+} // namespace stego
+
+using namespace stego;
+
+struct stego_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+uint64_t stego_batched_workspace_bytes(uint32_t n) { return workspace_bytes(n); }
+
+int stego_embed_batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results,
+                        uint32_t flags, const stego_tune *tune, void *d_ws, uint64_t ws_bytes,
+                        void *stream)
+{
+    return batched<true>(d_descs, n, d_results, flags, tune, d_ws, ws_bytes, stream);
+}
+
+int stego_extract_batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results,
+                          uint32_t flags, const stego_tune *tune, void *d_ws, uint64_t ws_bytes,
+                          void *stream)
+{
+    return batched<false>(d_descs, n, d_results, flags, tune, d_ws, ws_bytes, stream);
+}
+
+int stego_graph_capture_batched(int op, const stego_desc *d_descs, uint32_t n,
+                                stego_result *d_results, uint32_t flags, const stego_tune *tune,
+                                void *d_ws, uint64_t ws_bytes, stego_graph **out)
+{
+    if (!out || (op != STEGO_OP_EMBED_BATCHED && op != STEGO_OP_EXTRACT_BATCHED))
+        return STEGO_E_INVAL;
+    *out = nullptr;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+        return STEGO_E_CUDA;
+    int st = STEGO_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return STEGO_E_CUDA;
+    }
+    if (op == STEGO_OP_EMBED_BATCHED)
+        st = stego_embed_batched(d_descs, n, d_results, flags, tune, d_ws, ws_bytes, s);
+    else
+        st = stego_extract_batched(d_descs, n, d_results, flags, tune, d_ws, ws_bytes, s);
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
+    cudaStreamDestroy(s);
+    if (st != STEGO_OK) {
+        if (g)
+            cudaGraphDestroy(g);
+        return st;
+    }
+    if (ee != cudaSuccess || !g)
+        return STEGO_E_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return STEGO_E_CUDA;
+    }
+    stego_graph *h = new stego_graph;
+    h->graph = g;
+    h->exec = ex;
+    *out = h;
+    return STEGO_OK;
+}
+
+int stego_graph_launch(stego_graph *g, void *stream)
+{
+    if (!g)
+        return STEGO_E_INVAL;
+    return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? STEGO_OK : STEGO_E_CUDA;
+}
+
+int stego_graph_destroy(stego_graph *g)
+{
+    if (!g)
+        return STEGO_OK;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return STEGO_OK;
+}
+
+} // extern "C"

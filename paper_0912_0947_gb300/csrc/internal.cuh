@@ -1,0 +1,128 @@
+// internal.cuh -- declarations shared by the CUDA translation units of
+// libstego.so (not part of the public ABI; see include/stego.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "stego.h"
+
+namespace stego {
+
+// ---------------------------------------------------------------------------
+// Launch shapes
+// ---------------------------------------------------------------------------
+
+struct Shape {
+    int threads;         // threads per CTA
+    int vec;             // 16-byte vectors per thread per loop iteration
+    int ctas_per_sm;     // 0 = as many as occupancy allows
+    uint32_t tile_bytes; // batched: cover bytes per tile
+};
+
+// The shape installed for `op`, with the fields of `override_` (if non-null
+// and non-zero) taking precedence.
+Shape shape_for(int op, const stego_tune *override_);
+
+// Field ranges of a caller-supplied launch shape are valid.
+bool tune_ok(const stego_tune *t);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Persistent grid: min(ceil(units / units_per_cta), SMs * resident CTAs).
+// `kernel` is the __global__ function (for the occupancy query).
+int persistent_grid(const void *kernel, int threads, size_t smem, int ctas_per_sm,
+                    uint64_t units, uint64_t units_per_cta);
+
+// ---------------------------------------------------------------------------
+// Launchers (all stream-ordered, no synchronisation).  They return the CUDA
+// error of the launch.  `res` (nullable) receives msg_bytes = res_msg_bytes
+// and status STEGO_OK from block 0 of the launch; with `stats`, res->changed
+// and res->sse accumulate the changed-byte count and squared error and must
+// have been zeroed by the caller.
+// ---------------------------------------------------------------------------
+
+// STREAM1 embed.  n_bytes: bytes written (C out of place, T in place).
+// t_bytes: carrying bytes T = 8 * slen, slen = stream length in bytes
+// (message plus 4 header bytes when `header`).  nbits: the header value.
+cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uint64_t t_bytes,
+                     const uint8_t *msg, uint64_t slen, bool header, uint32_t nbits, bool stats,
+                     stego_result *res, uint64_t res_msg_bytes, const Shape &sh, cudaStream_t s);
+
+// STREAM1 extract.  With `header`, the length comes from the stego and all
+// fields of `res` (required) are written by block 0; otherwise raw_len bytes
+// are extracted and `res` is optional.
+cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
+                       uint64_t raw_len, bool header, stego_result *res, const Shape &sh,
+                       cudaStream_t s);
+
+// PAPER2 (Sections VI/VII), N > 0.  The embed writes only the 4N plane bytes
+// it carries: out of place the caller has copied the cover into stego first.
+cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
+                     const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
+                     const Shape &sh, cudaStream_t s);
+cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uint64_t N,
+                       stego_result *res, const Shape &sh, cudaStream_t s);
+
+// Changed-byte count and SSE of two arrays into out2[0..1] (zeroed by the
+// caller).
+cudaError_t changed_bytes(const uint8_t *a, const uint8_t *b, uint64_t n,
+                          unsigned long long *out2, const Shape &sh, cudaStream_t s);
+
+// One thread writes a whole result (calls that launch no other kernel).
+cudaError_t write_result(stego_result *res, uint64_t msg_bytes, int status, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Adds (a, b) of every thread of the block into out[0], out[1] with one pair
+// of 64-bit atomics per block.  All threads of the block must call it.
+__device__ __forceinline__ void block_add2(unsigned long long a, unsigned long long b,
+                                           unsigned long long *out)
+{
+    __shared__ unsigned long long sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = lane < nw ? sa[lane] : 0ull;
+        b = lane < nw ? sb[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+            b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+        }
+        if (lane == 0) {
+            if (a)
+                atomicAdd(out, a);
+            if (b)
+                atomicAdd(out + 1, b);
+        }
+    }
+}
+
+// Changed-byte count and squared error of one 32-bit word pair (four bytes).
+__device__ __forceinline__ void word_stats(uint32_t x, uint32_t y, unsigned long long &changed,
+                                           unsigned long long &sse)
+{
+    uint32_t d = x ^ y;
+    d |= d >> 4; // fold each byte's eight bits into its bit 0
+    d |= d >> 2;
+    d |= d >> 1;
+    changed += __popc(d & 0x01010101u);
+    const uint32_t a = __vabsdiffu4(x, y);
+    sse += __dp4a(a, a, 0u);
+}
+
+} // namespace stego

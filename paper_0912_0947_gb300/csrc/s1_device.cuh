@@ -1,0 +1,278 @@
+// s1_device.cuh -- device routines of the one-bit stream layout, shared by
+// the single-cover kernels (stream1.cu) and the persistent batched kernels
+// (batched.cu), so both run exactly the same per-vector code.
+//
+//   stego[k] = (cover[k] & 0xFE) | ((S[k/8] >> (7 - k%8)) & 1)   for k < T,
+//   stego[k] = cover[k]                                           for k >= T,
+//   S = BE32(8m) || msg (header) or S = msg,  T = 8|S|,
+//   msg[s] = sum_b (stego[base + 8s + b] & 1) << (7 - b),  base = 32 or 0.
+#pragma once
+
+#include "internal.cuh"
+
+namespace stego {
+namespace s1 {
+
+// One embedding job: cover/stego bytes [0, n_bytes) are written, bytes
+// below t_bytes carry stream bits.
+struct EmbedView {
+    const uint8_t *cover;
+    uint8_t *stego;
+    const uint8_t *msg;
+    uint64_t n_bytes; // bytes written (C out of place, T in place)
+    uint64_t t_bytes; // carrying bytes, 8 * slen
+    uint64_t slen;    // stream bytes
+    uint32_t header;  // S starts with BE32(nbits)
+    uint32_t nbits;
+    uint32_t msg_even; // msg pointer is 2-byte aligned
+    uint32_t pad;
+};
+
+// One extraction job: message bytes [0, len) from stego bytes starting at
+// `base` (32 behind a header, 0 otherwise).
+struct ExtractView {
+    const uint8_t *st;
+    uint8_t *msg;
+    uint64_t len;
+    uint64_t base;
+    uint32_t msg_even;
+    uint32_t pad;
+};
+
+// Byte q < slen of the stream S.
+__device__ __forceinline__ uint32_t stream_byte(const EmbedView &a, uint64_t q)
+{
+    if (a.header) {
+        if (q < 4)
+            return (a.nbits >> (24u - 8u * (uint32_t)q)) & 0xFFu;
+        return __ldg(a.msg + (q - 4));
+    }
+    return __ldg(a.msg + q);
+}
+
+// Stream bytes q and q+1 (q even) as S[q] | S[q+1] << 8; bytes at or past
+// slen read as 0.
+__device__ __forceinline__ uint32_t stream_pair(const EmbedView &a, uint64_t q)
+{
+    if (q + 1 < a.slen && (!a.header || q >= 4) && a.msg_even)
+        return __ldg(reinterpret_cast<const unsigned short *>(a.msg + (a.header ? q - 4 : q)));
+    uint32_t r = 0;
+    if (q < a.slen)
+        r = stream_byte(a, q);
+    if (q + 1 < a.slen)
+        r |= stream_byte(a, q + 1) << 8;
+    return r;
+}
+
+// The eight bits of a stream byte, most significant first, moved to bit 0 of
+// eight consecutive bytes.  `rep` holds the stream byte in all four byte
+// lanes (one __byte_perm).  Selecting bit 7-i in lane i and adding 0x7F to
+// every lane sets the lane's bit 7 exactly when the selected bit was set (no
+// carry leaves a lane); >> 7 brings it to bit 0.
+__device__ __forceinline__ uint32_t spread_hi(uint32_t rep)
+{ // cover bytes 0..3 <- bits 7..4
+    return (((rep & 0x10204080u) + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+}
+__device__ __forceinline__ uint32_t spread_lo(uint32_t rep)
+{ // cover bytes 4..7 <- bits 3..0
+    return (((rep & 0x01020408u) + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+}
+
+// 16-byte vectors v = v_first + i*step (+ u*blockDim.x for u < V), v < v_end,
+// of a job whose cover and stego are 16-byte aligned.  Each warp's 128-bit
+// load and store instructions cover 512 contiguous bytes.
+template <int V, bool STATS>
+__device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_first,
+                                                uint64_t v_end, uint64_t step,
+                                                unsigned long long &changed,
+                                                unsigned long long &sse)
+{
+    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.stego);
+    for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
+        uint4 c[V];
+        uint32_t p[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v < v_end)
+                c[u] = __ldcs(src + v);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            p[u] = 0;
+            if (v < v_end && (v << 4) < a.t_bytes)
+                p[u] = stream_pair(a, v << 1);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v >= v_end)
+                continue;
+            uint4 o = c[u];
+            const uint64_t k0 = v << 4;
+            if (k0 < a.t_bytes) {
+                const uint32_t r0 = __byte_perm(p[u], 0u, 0x0000u);
+                o.x = (c[u].x & 0xFEFEFEFEu) | spread_hi(r0);
+                o.y = (c[u].y & 0xFEFEFEFEu) | spread_lo(r0);
+                if (k0 + 8 < a.t_bytes) { // T is a multiple of 8
+                    const uint32_t r1 = __byte_perm(p[u], 0u, 0x1111u);
+                    o.z = (c[u].z & 0xFEFEFEFEu) | spread_hi(r1);
+                    o.w = (c[u].w & 0xFEFEFEFEu) | spread_lo(r1);
+                }
+            }
+            __stcs(dst + v, o);
+            if (STATS) {
+                word_stats(o.x, c[u].x, changed, sse);
+                word_stats(o.y, c[u].y, changed, sse);
+                word_stats(o.z, c[u].z, changed, sse);
+                word_stats(o.w, c[u].w, changed, sse);
+            }
+        }
+    }
+}
+
+// One byte k of a job (tails and unaligned buffers).
+template <bool STATS>
+__device__ __forceinline__ void embed_one(const EmbedView &a, uint64_t k, uint32_t s,
+                                          unsigned long long &changed, unsigned long long &sse)
+{
+    const uint32_t cb = a.cover[k];
+    uint32_t ob = cb;
+    if (k < a.t_bytes)
+        ob = (cb & 0xFEu) | ((s >> (7u - (uint32_t)(k & 7u))) & 1u);
+    a.stego[k] = (uint8_t)ob;
+    if (STATS) {
+        const uint32_t d = ob > cb ? ob - cb : cb - ob;
+        changed += d != 0;
+        sse += d * d;
+    }
+}
+
+// Bytes after the last whole vector (n_bytes % 16 of them), one per thread
+// of the calling CTA.
+template <bool STATS>
+__device__ __forceinline__ void embed_tail(const EmbedView &a, unsigned long long &changed,
+                                           unsigned long long &sse)
+{
+    if (threadIdx.x < (uint32_t)(a.n_bytes & 15u)) {
+        const uint64_t k = ((a.n_bytes >> 4) << 4) + threadIdx.x;
+        const uint32_t s = k < a.t_bytes ? stream_byte(a, k >> 3) : 0u;
+        embed_one<STATS>(a, k, s, changed, sse);
+    }
+}
+
+// Unaligned buffers: stream-byte units q = q_first + i*step (eight cover
+// bytes each), q < q_end.
+template <bool STATS>
+__device__ __forceinline__ void embed_bytes_range(const EmbedView &a, uint64_t q_first,
+                                                  uint64_t q_end, uint64_t step,
+                                                  unsigned long long &changed,
+                                                  unsigned long long &sse)
+{
+    for (uint64_t q = q_first; q < q_end; q += step) {
+        const uint32_t s = q < a.slen ? stream_byte(a, q) : 0u;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint64_t k = (q << 3) + b;
+            if (k >= a.n_bytes)
+                break;
+            embed_one<STATS>(a, k, s, changed, sse);
+        }
+    }
+}
+
+// Bit 0 of each byte of w, first byte as the most significant of a nibble.
+// (w & 0x01010101) has bits at 0, 8, 16, 24; the multiplier's terms
+// 2^27, 2^18, 2^9, 2^0 move them to bits 27, 26, 25, 24 and no other partial
+// product lands in bits 24..31.
+__device__ __forceinline__ uint32_t gather4(uint32_t w)
+{
+    return ((w & 0x01010101u) * 0x08040201u) >> 24;
+}
+
+// 16 stego bytes -> two message bytes, as m[2v] | m[2v+1] << 8.
+__device__ __forceinline__ uint32_t gather16(const uint4 &c)
+{
+    const uint32_t s0 = (gather4(c.x) << 4) | gather4(c.y);
+    const uint32_t s1 = (gather4(c.z) << 4) | gather4(c.w);
+    return s0 | (s1 << 8);
+}
+
+// Vectors v (16 stego bytes from base + 16v) -> message bytes 2v, 2v+1, for
+// v = v_first + i*step (+ u*blockDim.x), v < v_end; st + base 16-byte aligned.
+template <int V>
+__device__ __forceinline__ void extract_vec_range(const ExtractView &x, uint64_t v_first,
+                                                  uint64_t v_end, uint64_t step)
+{
+    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(x.st + x.base);
+    for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
+        uint4 c[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v < v_end)
+                c[u] = __ldcs(src + v);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v >= v_end)
+                continue;
+            const uint32_t pair = gather16(c[u]);
+            if (x.msg_even) {
+                *reinterpret_cast<unsigned short *>(x.msg + 2 * v) = (unsigned short)pair;
+            } else {
+                x.msg[2 * v] = (uint8_t)pair;
+                x.msg[2 * v + 1] = (uint8_t)(pair >> 8);
+            }
+        }
+    }
+}
+
+// Message byte q from its eight stego bytes (tails and unaligned stegos).
+__device__ __forceinline__ void extract_one(const ExtractView &x, uint64_t q)
+{
+    const uint8_t *p = x.st + x.base + (q << 3);
+    uint32_t s = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        s |= (uint32_t)(p[b] & 1u) << (7 - b);
+    x.msg[q] = (uint8_t)s;
+}
+
+__device__ __forceinline__ void extract_bytes_range(const ExtractView &x, uint64_t q_first,
+                                                    uint64_t q_end, uint64_t step)
+{
+    for (uint64_t q = q_first; q < q_end; q += step)
+        extract_one(x, q);
+}
+
+// Validity of a header value: the count must be whole bytes, fit the stego
+// after the 32 header bytes, and fit the caller's buffer.
+__device__ __forceinline__ int header_status(uint64_t C, uint64_t cap, uint32_t nbits)
+{
+    if (C < 32)
+        return STEGO_E_BAD_HEADER;
+    if (nbits & 7u)
+        return STEGO_E_BAD_HEADER;
+    if (32ull + nbits > C)
+        return STEGO_E_BAD_HEADER;
+    if ((uint64_t)(nbits >> 3) > cap)
+        return STEGO_E_MSG_TOO_SMALL;
+    return STEGO_OK;
+}
+
+// The 32-bit header, read by one whole warp: lane l loads stego byte l and a
+// ballot of the LSBs gives the header bits with bit l = header bit 31-l, so
+// the count is the bit-reversed ballot.  Every lane gets the value.
+__device__ __forceinline__ uint32_t warp_read_header(const uint8_t *st, uint64_t C)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t byte = (lane < C) ? (uint32_t)st[lane] : 0u;
+    return __brev(__ballot_sync(0xFFFFFFFFu, byte & 1u));
+}
+
+} // namespace s1
+} // namespace stego

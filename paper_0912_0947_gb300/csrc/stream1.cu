@@ -1,0 +1,231 @@
+// stream1.cu -- single-cover kernels of the one-bit stream layout: the
+// Section VI substitution rule with one bit per cover byte over the cover in
+// memory order, and the Section VII extraction of the same bits.
+//
+// Data layout and traffic: a 16-byte cover vector v carries stream bytes 2v
+// and 2v+1, so one warp's 128-bit load instruction covers 512 contiguous
+// cover bytes and its message reads cover 64 contiguous stream bytes.  Out of
+// place an embed moves 2C + T/8 bytes, in place 2T + T/8, an extract T + T/8
+// (T = carrying bytes).  Each byte is read once and written once, so nothing
+// is staged through shared memory: 128-bit streaming loads/stores with V
+// vectors in flight per thread over a persistent grid feed HBM directly.
+#include "s1_device.cuh"
+
+namespace stego {
+namespace {
+
+using s1::EmbedView;
+using s1::ExtractView;
+
+struct EmbedArgs {
+    EmbedView a;
+    stego_result *res;
+    uint64_t res_msg_bytes;
+};
+
+__device__ __forceinline__ void write_res(const EmbedArgs &e, bool stats)
+{
+    if (e.res && blockIdx.x == 0 && threadIdx.x == 0) {
+        e.res->msg_bytes = e.res_msg_bytes;
+        e.res->status = STEGO_OK;
+        e.res->reserved = 0;
+        if (!stats) {
+            e.res->changed = 0;
+            e.res->sse = 0;
+        }
+    }
+}
+
+// Vector path (cover and stego 16-byte aligned), persistent grid.
+template <int V, bool STATS>
+__global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
+{
+    unsigned long long changed = 0, sse = 0;
+    write_res(e, STATS);
+    s1::embed_vec_range<V, STATS>(e.a, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x,
+                                  e.a.n_bytes >> 4, (uint64_t)gridDim.x * blockDim.x * V,
+                                  changed, sse);
+    if (blockIdx.x == 0)
+        s1::embed_tail<STATS>(e.a, changed, sse);
+    if (STATS)
+        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&e.res->changed));
+}
+
+// Byte path for buffers that are not 16-byte aligned: one thread per stream
+// byte (eight cover bytes).
+template <bool STATS>
+__global__ void __launch_bounds__(512) embed_bytes(EmbedArgs e)
+{
+    unsigned long long changed = 0, sse = 0;
+    write_res(e, STATS);
+    s1::embed_bytes_range<STATS>(e.a, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                 (e.a.n_bytes + 7) >> 3, (uint64_t)gridDim.x * blockDim.x,
+                                 changed, sse);
+    if (STATS)
+        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&e.res->changed));
+}
+
+struct ExtractArgs {
+    const uint8_t *st;
+    uint64_t C;
+    uint8_t *msg;
+    uint64_t cap;
+    uint64_t raw_len;
+    uint32_t header;
+    uint32_t msg_even;
+    stego_result *res;
+};
+
+// Length and status of the call: from the header (read by warp 0 of every
+// CTA with one ballot) or the caller's length.  Block 0 publishes them.
+__device__ __forceinline__ int extract_prologue(const ExtractArgs &a, ExtractView &x)
+{
+    __shared__ int s_status;
+    __shared__ unsigned long long s_len;
+    x.st = a.st;
+    x.msg = a.msg;
+    x.msg_even = a.msg_even;
+    x.pad = 0;
+    if (a.header) {
+        if (threadIdx.x < 32) {
+            const uint32_t nbits = s1::warp_read_header(a.st, a.C);
+            if (threadIdx.x == 0) {
+                const int st = s1::header_status(a.C, a.cap, nbits);
+                s_status = st;
+                s_len = st == STEGO_OK ? (nbits >> 3) : 0u;
+            }
+        }
+        __syncthreads();
+        x.len = s_len;
+        x.base = 32;
+    } else {
+        if (threadIdx.x == 0) {
+            s_status = STEGO_OK;
+            s_len = a.raw_len;
+        }
+        __syncthreads();
+        x.len = a.raw_len;
+        x.base = 0;
+    }
+    const int status = s_status;
+    if (a.res && blockIdx.x == 0 && threadIdx.x == 0) {
+        a.res->changed = 0;
+        a.res->sse = 0;
+        a.res->msg_bytes = x.len;
+        a.res->status = status;
+        a.res->reserved = 0;
+    }
+    return status;
+}
+
+// Vector path: stego 16-byte aligned.
+template <int V>
+__global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
+{
+    ExtractView x;
+    if (extract_prologue(a, x) != STEGO_OK)
+        return;
+    s1::extract_vec_range<V>(x, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x, x.len >> 1,
+                             (uint64_t)gridDim.x * blockDim.x * V);
+    if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0)
+        s1::extract_one(x, x.len - 1);
+}
+
+// Byte path for a stego that is not 16-byte aligned: one thread per message
+// byte.
+__global__ void __launch_bounds__(512) extract_bytes(ExtractArgs a)
+{
+    ExtractView x;
+    if (extract_prologue(a, x) != STEGO_OK)
+        return;
+    s1::extract_bytes_range(x, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, x.len,
+                            (uint64_t)gridDim.x * blockDim.x);
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int clamp_vec(int v) { return (v == 1 || v == 2 || v == 8) ? v : 4; }
+
+} // namespace
+
+cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uint64_t t_bytes,
+                     const uint8_t *msg, uint64_t slen, bool header, uint32_t nbits, bool stats,
+                     stego_result *res, uint64_t res_msg_bytes, const Shape &sh, cudaStream_t s)
+{
+    EmbedArgs e;
+    e.a.cover = cover;
+    e.a.stego = stego;
+    e.a.msg = msg;
+    e.a.n_bytes = n_bytes;
+    e.a.t_bytes = t_bytes;
+    e.a.slen = slen;
+    e.a.header = header ? 1u : 0u;
+    e.a.nbits = nbits;
+    e.a.msg_even = ((uintptr_t)msg & 1u) == 0;
+    e.a.pad = 0;
+    e.res = res;
+    e.res_msg_bytes = res_msg_bytes;
+    const int T = sh.threads;
+    void *args[] = {&e};
+    if (aligned16(cover) && aligned16(stego)) {
+        const int vec = clamp_vec(sh.vec);
+        const void *k = nullptr;
+        switch (vec) {
+        case 1: k = stats ? (const void *)embed_vec<1, true> : (const void *)embed_vec<1, false>; break;
+        case 2: k = stats ? (const void *)embed_vec<2, true> : (const void *)embed_vec<2, false>; break;
+        case 8: k = stats ? (const void *)embed_vec<8, true> : (const void *)embed_vec<8, false>; break;
+        default: k = stats ? (const void *)embed_vec<4, true> : (const void *)embed_vec<4, false>; break;
+        }
+        const uint64_t nvec = n_bytes >> 4;
+        const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvec > 0 ? nvec : 1,
+                                         (uint64_t)T * vec);
+        return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    }
+    const void *k = stats ? (const void *)embed_bytes<true> : (const void *)embed_bytes<false>;
+    const uint64_t units = (n_bytes + 7) >> 3;
+    const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, units > 0 ? units : 1, (uint64_t)T);
+    return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+}
+
+cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
+                       uint64_t raw_len, bool header, stego_result *res, const Shape &sh,
+                       cudaStream_t s)
+{
+    ExtractArgs a;
+    a.st = st;
+    a.C = C;
+    a.msg = msg;
+    a.cap = cap;
+    a.raw_len = raw_len;
+    a.header = header ? 1u : 0u;
+    a.msg_even = ((uintptr_t)msg & 1u) == 0;
+    a.res = res;
+    // the longest message the launch may have to produce
+    uint64_t max_len = raw_len;
+    if (header) {
+        const uint64_t fit = C >= 32 ? (C - 32) / 8 : 0;
+        max_len = fit < cap ? fit : cap;
+    }
+    const int T = sh.threads;
+    void *args[] = {&a};
+    if (aligned16(st)) {
+        const int vec = clamp_vec(sh.vec);
+        const void *k;
+        switch (vec) {
+        case 1: k = (const void *)extract_vec<1>; break;
+        case 2: k = (const void *)extract_vec<2>; break;
+        case 8: k = (const void *)extract_vec<8>; break;
+        default: k = (const void *)extract_vec<4>; break;
+        }
+        const uint64_t nvec = max_len >> 1;
+        const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvec > 0 ? nvec : 1,
+                                         (uint64_t)T * vec);
+        return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    }
+    const void *k = (const void *)extract_bytes;
+    const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, max_len > 0 ? max_len : 1,
+                                     (uint64_t)T);
+    return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+}
+
+} // namespace stego

@@ -1,0 +1,102 @@
+"""The C-ABI library builds, loads and exports every function that
+include/stego.h declares; host-only entry points (no device work) behave as
+documented.  Runs without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_0912_0947_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    try:
+        B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    return B.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "stego.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(stego_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("stego_embed", "stego_extract", "stego_embed_batched", "stego_extract_batched",
+              "stego_changed_bytes", "stego_capacity", "stego_strerror",
+              "stego_batched_workspace_bytes"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function(built):
+    lib = ctypes.CDLL(built)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(built):
+    import paper_0912_0947_gb300 as S
+    assert S.stego_version() >= 10000
+    assert S.strerror(S.E_BAD_HEADER) == "bad or missing length header"
+    # capacities: floor(C/8) - 4 with the header, floor(C/8) raw, floor(W/4)*H
+    assert S.stego_capacity(201326592, S.HEADER_BE32) == 25165820
+    assert S.stego_capacity(786432, S.HEADER_BE32) == 98300
+    assert S.stego_capacity(31, S.HEADER_BE32) == 0
+    assert S.stego_capacity(41, 0) == 5
+    assert S.stego_capacity(1024, S.LAYOUT_PAPER2, (1024, 1, 1, 0)) == 256
+    assert S.stego_capacity(7 * 5 * 3, S.LAYOUT_PAPER2, (7, 5, 3, 2)) == 5
+    with pytest.raises(S.StegoError):
+        S.stego_capacity(100, S.LAYOUT_PAPER2, (7, 5, 3, 3))  # plane >= channels
+    with pytest.raises(S.StegoError):
+        S.stego_capacity(100, S.LAYOUT_PAPER2, (7, 5, 3, 0))  # size mismatch
+    assert S.stego_batched_workspace_bytes(0) >= 64
+    assert S.stego_batched_workspace_bytes(4096) >= 64 + 8 * 4097 + 32 * 4096
+
+
+def test_tune_validation(built):
+    import paper_0912_0947_gb300 as S
+    old = S.stego_get_tune(S.OP_EMBED)
+    with pytest.raises(S.StegoError):
+        S.stego_set_tune(S.OP_EMBED, (100, 4, 0, 0))   # not a multiple of 32
+    with pytest.raises(S.StegoError):
+        S.stego_set_tune(S.OP_EMBED, (256, 3, 0, 0))   # vec not in {1,2,4,8}
+    with pytest.raises(S.StegoError):
+        S.stego_set_tune(S.OP_EMBED_BATCHED, (256, 4, 0, 5000))  # tile not 4 KiB multiple
+    with pytest.raises(S.StegoError):
+        S.stego_set_tune(9, (256, 4, 0, 0))
+    S.stego_set_tune(S.OP_EMBED, (128, 2, 3, 0))
+    t = S.stego_get_tune(S.OP_EMBED)
+    assert (t.threads, t.vec_per_thread, t.ctas_per_sm) == (128, 2, 3)
+    S.stego_set_tune(S.OP_EMBED, old)
+
+
+def test_struct_sizes_match_header():
+    import paper_0912_0947_gb300 as S
+    assert S.DESC_DTYPE.itemsize == 72
+    assert ctypes.sizeof(S.Geom) == 16 and ctypes.sizeof(S.Tune) == 16
+
+
+def test_binding_refuses_cpu_tensors(built):
+    import torch
+    import paper_0912_0947_gb300 as S
+    c = torch.zeros(64, dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        S.stego_embed(c, c.clone(), torch.zeros(1, dtype=torch.uint8), S.HEADER_BE32)
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_0912_0947_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "stego_oracle" not in text, f

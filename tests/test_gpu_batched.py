@@ -1,0 +1,226 @@
+"""GPU parity of the persistent batched path: every descriptor's output and
+result equal the oracle's and the single-cover call's, including covers of
+uneven sizes, in-place and misaligned buffers, empty covers and per-cover
+errors; a captured CUDA graph replays the same work."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import need_gpu
+from paper_0912_0947_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def O():
+    return oracle.load()
+
+
+class Arena:
+    """One device buffer holding many covers at chosen offsets."""
+
+    def __init__(self, sizes, offs, fill=None, device="cuda"):
+        self.pos = []
+        p = 0
+        for n, o in zip(sizes, offs):
+            p = (p + 255) // 256 * 256 + o
+            self.pos.append(p)
+            p += n
+        self.buf = torch.zeros(p + 256, dtype=torch.uint8, device=device)
+        self.sizes = list(sizes)
+        if fill is not None:
+            for i, a in enumerate(fill):
+                self.view(i).copy_(torch.from_numpy(np.ascontiguousarray(a)).to(device))
+
+    def view(self, i):
+        return self.buf[self.pos[i]: self.pos[i] + self.sizes[i]]
+
+
+def _mixed_batch(rng, count):
+    items = []
+    for i in range(count):
+        C = int(rng.choice([0, 7, 31, 32, 40, 4096, 65536, 65536 * 3 + 17,
+                            int(rng.integers(1, 300000))]))
+        header = bool(rng.integers(0, 2))
+        cap = max(C // 8 - (4 if header else 0), 0)
+        if header and C < 32:
+            m = 0
+        else:
+            m = int(rng.integers(0, cap + 1)) if cap else 0
+        if i % 11 == 5:
+            m = cap + 1  # a capacity error for this cover only
+        items.append(dict(C=C, header=header, m=m,
+                          inplace=bool(i % 3 == 0),
+                          coff=int(rng.choice([0, 0, 0, 5])),
+                          moff=int(rng.choice([0, 1]))))
+    return items
+
+
+def _run_embed(S, items, rng, stats=True):
+    covers = [rng.integers(0, 256, it["C"], dtype=np.uint8) for it in items]
+    msgs = [rng.integers(0, 256, it["m"], dtype=np.uint8) for it in items]
+    ca = Arena([it["C"] for it in items], [it["coff"] for it in items], covers)
+    sa = Arena([it["C"] for it in items], [it["coff"] for it in items])
+    ma = Arena([it["m"] for it in items], [it["moff"] for it in items], msgs)
+    recs = []
+    for i, it in enumerate(items):
+        st = ca.view(i) if it["inplace"] else sa.view(i)
+        recs.append(dict(cover=ca.view(i), stego=st, msg=ma.view(i), cover_bytes=it["C"],
+                         msg_bytes=it["m"], flags=S.HEADER_BE32 if it["header"] else 0))
+    descs = S.descs_to_device(S.pack_descs(recs))
+    n = len(items)
+    res = S.new_result(n=n)
+    ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(descs, n, res, S.FUSE_STATS if stats else 0, ws)
+    torch.cuda.synchronize()
+    outs = [(ca.view(i) if it["inplace"] else sa.view(i)) for i, it in enumerate(items)]
+    return covers, msgs, outs, S.read_result(res), (ca, sa, ma, descs, res, ws)
+
+
+def test_batched_embed_extract_matches_oracle(S, O):
+    rng = np.random.default_rng(21)
+    items = _mixed_batch(rng, 120)
+    covers, msgs, outs, results, keep = _run_embed(S, items, rng)
+    stegos = []
+    for i, it in enumerate(items):
+        st, want = O.stream1_embed(covers[i], msgs[i], header=it["header"])
+        r = results[i]
+        assert r["status"] == st, (i, it, r)
+        if st != oracle.OK:
+            assert r["msg_bytes"] == 0
+            stegos.append(None)
+            continue
+        got = outs[i].cpu().numpy()
+        assert np.array_equal(got, want), (i, it)
+        assert (r["changed"], r["sse"]) == O.changed_bytes(covers[i], want)
+        assert r["msg_bytes"] == it["m"]
+        stegos.append(want)
+    # batched extraction of the same covers into stale buffers
+    ok = [i for i in range(len(items)) if stegos[i] is not None]
+    sizes = [items[i]["C"] for i in ok]
+    sa = Arena(sizes, [items[i]["coff"] for i in ok], [stegos[i] for i in ok])
+    caps = [items[i]["m"] + 2 for i in ok]
+    ma = Arena(caps, [items[i]["moff"] for i in ok], [np.full(c, 0xEE, np.uint8) for c in caps])
+    recs = [dict(cover=sa.view(j), msg=ma.view(j), cover_bytes=sizes[j], msg_bytes=caps[j],
+                 msg_len=items[i]["m"], flags=S.HEADER_BE32 if items[i]["header"] else 0)
+            for j, i in enumerate(ok)]
+    descs = S.descs_to_device(S.pack_descs(recs))
+    res = S.new_result(n=len(ok))
+    ws = torch.empty(S.stego_batched_workspace_bytes(len(ok)), dtype=torch.uint8, device="cuda")
+    S.stego_extract_batched(descs, len(ok), res, 0, ws)
+    rr = S.read_result(res)
+    for j, i in enumerate(ok):
+        assert rr[j]["status"] == 0 and rr[j]["msg_bytes"] == items[i]["m"], (i, rr[j])
+        got = ma.view(j).cpu().numpy()
+        assert np.array_equal(got[: items[i]["m"]], msgs[i])
+        assert np.all(got[items[i]["m"]:] == 0xEE)
+
+
+def test_batched_equals_single_calls_and_graph_replay(S):
+    rng = np.random.default_rng(22)
+    items = [dict(C=int(c), header=True, m=int(c) // 8 - 4 - int(k), inplace=False, coff=0, moff=0)
+             for c, k in zip(rng.integers(40, 2_000_000, 64), rng.integers(0, 5, 64))]
+    covers, msgs, outs, results, keep = _run_embed(S, items, rng)
+    for i, it in enumerate(items):
+        c = torch.from_numpy(covers[i]).cuda()
+        s = torch.empty_like(c)
+        r = S.new_result()
+        S.stego_embed(c, s, torch.from_numpy(msgs[i]).cuda(), S.HEADER_BE32 | S.FUSE_STATS, r)
+        assert torch.equal(s, outs[i]), i
+        one = S.read_result(r)
+        assert (one["changed"], one["sse"]) == (results[i]["changed"], results[i]["sse"])
+    ca, sa, ma, descs, res, ws = keep
+    g = S.BatchedGraph(S.OP_EMBED_BATCHED, descs, len(items), res, S.FUSE_STATS, ws)
+    sa.buf.zero_()
+    res.zero_()
+    g.launch()
+    g.launch()  # replays are idempotent
+    torch.cuda.synchronize()
+    again = S.read_result(res)
+    for i in range(len(items)):
+        assert torch.equal(sa.view(i), outs[i])
+        assert again[i] == results[i]
+    g.close()
+
+
+@pytest.mark.parametrize("tile,threads,vec", [(4096, 64, 1), (65536, 256, 4), (1 << 20, 512, 8),
+                                              (12288, 128, 2)])
+def test_batched_launch_shapes(S, O, tile, threads, vec):
+    rng = np.random.default_rng(tile + threads)
+    items = _mixed_batch(rng, 40)
+    covers = [rng.integers(0, 256, it["C"], dtype=np.uint8) for it in items]
+    msgs = [rng.integers(0, 256, it["m"], dtype=np.uint8) for it in items]
+    ca = Arena([it["C"] for it in items], [it["coff"] for it in items], covers)
+    sa = Arena([it["C"] for it in items], [it["coff"] for it in items])
+    ma = Arena([it["m"] for it in items], [it["moff"] for it in items], msgs)
+    recs = [dict(cover=ca.view(i), stego=sa.view(i), msg=ma.view(i), cover_bytes=it["C"],
+                 msg_bytes=it["m"], flags=S.HEADER_BE32 if it["header"] else 0)
+            for i, it in enumerate(items)]
+    descs = S.descs_to_device(S.pack_descs(recs))
+    res = S.new_result(n=len(items))
+    ws = torch.empty(S.stego_batched_workspace_bytes(len(items)), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(descs, len(items), res, S.FUSE_STATS, ws, tune=(threads, vec, 0, tile))
+    rr = S.read_result(res)
+    for i, it in enumerate(items):
+        st, want = O.stream1_embed(covers[i], msgs[i], header=it["header"])
+        assert rr[i]["status"] == st
+        if st == 0:
+            assert np.array_equal(sa.view(i).cpu().numpy(), want)
+
+
+def test_batched_argument_errors(S):
+    descs = torch.zeros(72, dtype=torch.uint8, device="cuda")
+    res = S.new_result(n=1)
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.StegoError) as e:
+        S.stego_embed_batched(descs, 1, res, 0, ws)
+    assert e.value.status == S.E_NOMEM
+    ws = torch.empty(S.stego_batched_workspace_bytes(1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.StegoError) as e:
+        S.stego_extract_batched(descs, 1, res, S.FUSE_STATS, ws)
+    assert e.value.status == S.E_INVAL
+    # an all-zero descriptor is an empty cover: ok, nothing to do
+    S.stego_embed_batched(descs, 1, res, 0, ws)
+    assert S.read_result(res)[0]["status"] == 0
+
+
+def test_video_frames(S, O):
+    """600 frames of 1920x1080x3 (gradient plus noise), one message stream
+    split across frames at half capacity with a per-frame header, all frames
+    in one batched launch; sampled frames against the oracle, every frame's
+    round trip on the device."""
+    v = synth.Video()
+    F, fb, P = v.frames, v.frame_bytes, v.per_frame_msg
+    frames = v.frame_range(0, F, "cuda").view(F, fb)
+    stream = v.message("cuda")
+    stego = torch.empty_like(frames)
+    recs = [dict(cover=frames[f], stego=stego[f], msg=stream[f * P:(f + 1) * P], cover_bytes=fb,
+                 msg_bytes=P, flags=S.HEADER_BE32) for f in range(F)]
+    descs = S.descs_to_device(S.pack_descs(recs))
+    res = S.new_result(n=F)
+    ws = torch.empty(S.stego_batched_workspace_bytes(F), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(descs, F, res, S.FUSE_STATS, ws)
+    rr = S.read_result(res)
+    assert all(r["status"] == 0 and r["msg_bytes"] == P for r in rr)
+    for f in (0, 1, 299, 598, 599):
+        c = frames[f].cpu().numpy()
+        st, want = O.stream1_embed(c, stream[f * P:(f + 1) * P].cpu().numpy(), header=True)
+        assert st == 0 and np.array_equal(stego[f].cpu().numpy(), want), f
+        assert (rr[f]["changed"], rr[f]["sse"]) == O.changed_bytes(c, want)
+    # properties on every frame: only LSBs change, nothing past T changes
+    T = 8 * (P + 4)
+    assert not bool(((stego ^ frames) & 0xFE).any())
+    assert torch.equal(stego[:, T:], frames[:, T:])
+    out = torch.empty(F * P, dtype=torch.uint8, device="cuda")
+    recs = [dict(cover=stego[f], msg=out[f * P:(f + 1) * P], cover_bytes=fb, msg_bytes=P,
+                 flags=S.HEADER_BE32) for f in range(F)]
+    descs = S.descs_to_device(S.pack_descs(recs))
+    S.stego_extract_batched(descs, F, res, 0, ws)
+    assert torch.equal(out, stream), "concatenated per-frame extracts give the stream back"

@@ -1,0 +1,260 @@
+"""GPU parity of the one-bit stream layout (embed, extract, fused changed/SSE)
+against the CPU oracle, byte for byte, through the C ABI.
+
+Sizes span several grid-stride iterations and ragged tails; misaligned
+buffers exercise the byte paths; canary bytes around every output catch
+out-of-bounds writes (compute-sanitizer is not used)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle_pins as P
+from gpu_util import Guarded, dev, need_gpu
+from paper_0912_0947_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [0, 1, 8, 15, 16, 17, 31, 32, 33, 39, 40, 41, 47, 48, 100, 4095, 4096, 4097,
+         65543, (1 << 20) + 13, 3 * 16384 * 9 + 8]
+
+
+@pytest.fixture(scope="module")
+def S():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def O():
+    return oracle.load()
+
+
+def _msgs(cap, rng):
+    out = []
+    for m in sorted({0, 1, cap // 2, cap}):
+        if 0 <= m <= cap:
+            out.append(rng.integers(0, 256, m, dtype=np.uint8))
+    return out
+
+
+def _embed_check(S, O, cover, msg, header, offs=(0, 0, 0), inplace=False):
+    C = cover.size
+    flags = (S.HEADER_BE32 if header else 0) | S.FUSE_STATS
+    st_o, want = O.stream1_embed(cover, msg, header=header)
+    if st_o != oracle.OK:
+        gc = Guarded(C, offs[0], cover)
+        gs = Guarded(C, offs[1], 0x5A)
+        with pytest.raises(S.StegoError) as e:
+            S.stego_embed(gc.view, gs.view, dev(msg), flags, S.new_result())
+        assert e.value.status == st_o
+        assert np.all(gs.host() == 0x5A) and gs.canaries_intact()
+        return None
+    gc = Guarded(C, offs[0], cover)
+    gm = Guarded(msg.size, offs[2], msg)
+    res = S.new_result()
+    if inplace:
+        S.stego_embed(gc.view, gc.view, gm.view, flags, res)
+        out = gc
+    else:
+        gs = Guarded(C, offs[1], 0x5A)
+        S.stego_embed(gc.view, gs.view, gm.view, flags, res)
+        out = gs
+    got = out.host()
+    assert np.array_equal(got, want), (C, msg.size, header, offs, inplace)
+    assert out.canaries_intact()
+    assert gm.canaries_intact() and np.array_equal(gm.host(), msg)
+    if not inplace:
+        assert np.array_equal(gc.host(), cover) and gc.canaries_intact()
+    r = S.read_result(res)
+    assert r["status"] == 0 and r["msg_bytes"] == msg.size
+    assert (r["changed"], r["sse"]) == O.changed_bytes(cover, want)
+    return want
+
+
+def _extract_check(S, O, stego, m, header, offs=(0, 0)):
+    C = stego.size
+    cap = m + 3
+    st_o, want = O.stream1_extract(stego, cap=cap, header=header, raw_len=m)
+    assert st_o == oracle.OK
+    gs = Guarded(C, offs[0], stego)
+    gm = Guarded(cap, offs[1], 0xEE)
+    res = S.new_result()
+    S.stego_extract(gs.view, gm.view, m, S.HEADER_BE32 if header else 0, res)
+    r = S.read_result(res)
+    assert r["status"] == 0 and r["msg_bytes"] == want.size
+    got = gm.host()
+    assert np.array_equal(got[: want.size], want)
+    assert np.all(got[want.size:] == 0xEE), "bytes past the message untouched"
+    assert gm.canaries_intact() and gs.canaries_intact()
+
+
+@pytest.mark.parametrize("C", SIZES)
+@pytest.mark.parametrize("header", [True, False])
+def test_sizes_aligned(S, O, C, header):
+    rng = np.random.default_rng(C * 2 + header)
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    cap = S.stego_capacity(C, S.HEADER_BE32 if header else 0)
+    for msg in _msgs(cap, rng):
+        for inplace in (False, True):
+            stego = _embed_check(S, O, cover, msg, header, inplace=inplace)
+        if stego is not None:
+            _extract_check(S, O, stego, msg.size, header)
+
+
+@pytest.mark.parametrize("offs", [(1, 1, 0), (3, 7, 1), (8, 8, 3), (0, 5, 0), (15, 0, 2)])
+@pytest.mark.parametrize("C", [17, 100, 4097, 70001])
+def test_misaligned_buffers(S, O, C, offs):
+    rng = np.random.default_rng(C + sum(offs))
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    for header in (True, False):
+        cap = S.stego_capacity(C, S.HEADER_BE32 if header else 0)
+        for msg in _msgs(cap, rng):
+            stego = _embed_check(S, O, cover, msg, header, offs=offs)
+            _embed_check(S, O, cover, msg, header, offs=offs, inplace=True)
+            if stego is not None:
+                _extract_check(S, O, stego, msg.size, header, offs=(offs[1], offs[2]))
+
+
+def test_hand_examples(S, O):
+    for name in ("stream1_raw_a5.txt", "stream1_header_a5.txt"):
+        g = P.load_golden(name)
+        got = _embed_check(S, O, g["cover"], g["msg"], bool(g["header"]))
+        assert got.tolist() == g["stego"].tolist()
+
+
+def test_bad_headers_reported_on_device(S):
+    g = P.load_golden("stream1_bad_header.txt")
+    cases = [(g["stego"], 64, S.E_BAD_HEADER)]
+    rng = np.random.default_rng(5)
+    c = rng.integers(0, 256, 64, dtype=np.uint8)
+    for nbits, cap, want in ((40, 100, S.E_BAD_HEADER), (32, 3, S.E_MSG_TOO_SMALL),
+                             (32, 4, S.OK), (0, 0, S.OK)):
+        x = c.copy()
+        h = format(nbits, "032b")
+        for k in range(32):
+            x[k] = (x[k] & 0xFE) | int(h[k])
+        cases.append((x, cap, want))
+    cases.append((c[:31], 100, S.E_BAD_HEADER))
+    cases.append((c[:0], 100, S.E_BAD_HEADER))
+    for stego, cap, want in cases:
+        gs = Guarded(stego.size, 0, stego)
+        gm = Guarded(max(cap, 1), 0, 0xEE)
+        res = S.new_result()
+        S.stego_extract(gs.view, gm.view[:cap], 0, S.HEADER_BE32, res)
+        r = S.read_result(res)
+        assert r["status"] == want, (stego.size, cap, r)
+        if want != S.OK:
+            assert r["msg_bytes"] == 0
+            assert np.all(gm.host() == 0xEE), "message untouched on error"
+        assert gm.canaries_intact()
+
+
+def test_capacity_and_argument_errors(S):
+    cover = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    stego = torch.full((64,), 0x77, dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.StegoError) as e:
+        S.stego_embed(cover, stego, torch.zeros(5, dtype=torch.uint8, device="cuda"), S.HEADER_BE32)
+    assert e.value.status == S.E_CAPACITY
+    torch.cuda.synchronize()
+    assert bool((stego == 0x77).all()), "nothing written on a capacity error"
+    with pytest.raises(S.StegoError) as e:
+        S.stego_extract(cover, torch.zeros(8, dtype=torch.uint8, device="cuda"), 9, 0)
+    assert e.value.status == S.E_CAPACITY
+    with pytest.raises(S.StegoError) as e:
+        S.stego_extract(cover, torch.zeros(2, dtype=torch.uint8, device="cuda"), 3, 0)
+    assert e.value.status == S.E_MSG_TOO_SMALL
+    with pytest.raises(S.StegoError) as e:  # overlapping cover and stego (not in place)
+        S.stego_embed(cover[:48], cover[8:56], torch.zeros(1, dtype=torch.uint8, device="cuda"), 0)
+    assert e.value.status == S.E_INVAL
+    with pytest.raises(S.StegoError) as e:  # stats need a result
+        S.stego_embed(cover, stego, torch.zeros(1, dtype=torch.uint8, device="cuda"), S.FUSE_STATS)
+    assert e.value.status == S.E_INVAL
+    with pytest.raises(S.StegoError) as e:  # header extraction needs a result
+        S.stego_extract(cover, torch.zeros(8, dtype=torch.uint8, device="cuda"), 0, S.HEADER_BE32)
+    assert e.value.status == S.E_INVAL
+
+
+def test_launch_shapes_agree(S, O):
+    """Every launch shape the tuner may pick gives the oracle's bytes."""
+    rng = np.random.default_rng(9)
+    C = 3 * 65536 + 40
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    msg = rng.integers(0, 256, C // 8 - 4 - 3, dtype=np.uint8)
+    old_e, old_x = S.stego_get_tune(S.OP_EMBED), S.stego_get_tune(S.OP_EXTRACT)
+    try:
+        for threads in (64, 128, 256, 512):
+            for vec in (1, 2, 4, 8):
+                for cps in (0, 1, 3):
+                    S.stego_set_tune(S.OP_EMBED, (threads, vec, cps, 0))
+                    S.stego_set_tune(S.OP_EXTRACT, (threads, vec, cps, 0))
+                    stego = _embed_check(S, O, cover, msg, True)
+                    _extract_check(S, O, stego, msg.size, True)
+    finally:
+        S.stego_set_tune(S.OP_EMBED, old_e)
+        S.stego_set_tune(S.OP_EXTRACT, old_x)
+
+
+def test_changed_bytes(S, O):
+    rng = np.random.default_rng(10)
+    for n in (0, 1, 15, 16, 17, 1000, 65536 + 7, 1 << 20):
+        a = rng.integers(0, 256, n, dtype=np.uint8)
+        b = a.copy()
+        idx = rng.integers(0, max(n, 1), n // 3)
+        if n:
+            b[idx] = rng.integers(0, 256, idx.size, dtype=np.uint8)
+        for off in (0, 3):
+            ga, gb = Guarded(n, off, a), Guarded(n, 0, b)
+            out = torch.zeros(2, dtype=torch.int64, device="cuda")
+            S.stego_changed_bytes(ga.view, gb.view, out)
+            assert tuple(out.cpu().tolist()) == O.changed_bytes(a, b), (n, off)
+
+
+def test_single_512_round_trip(S, O):
+    """512x512x3 uniform cover, 32768-byte message behind the header."""
+    w = synth.single_512()
+    cover = w.cover("cuda")
+    msg = w.message("cuda")
+    stego = torch.empty_like(cover)
+    res = S.new_result()
+    S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res)
+    c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+    st, want = O.stream1_embed(c_h, m_h, header=True)
+    assert st == 0 and np.array_equal(stego.cpu().numpy(), want)
+    r = S.read_result(res)
+    assert (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+    out = torch.empty(w.msg_bytes + 16, dtype=torch.uint8, device="cuda")
+    res2 = S.new_result()
+    S.stego_extract(stego, out, 0, S.HEADER_BE32, res2)
+    r2 = S.read_result(res2)
+    assert r2["status"] == 0 and r2["msg_bytes"] == w.msg_bytes
+    assert torch.equal(out[: w.msg_bytes], msg)
+    psnr = oracle.psnr(r["sse"], cover.numel())
+    assert 55.0 < psnr < 57.0  # about half of 262176 carried LSBs flip
+
+
+def test_single_8192_full_capacity(S, O):
+    """The 8192x8192x3 cover at full one-bit capacity, in the launch shape
+    the benchmark uses, compared with the oracle over every byte."""
+    w = synth.single_8192()
+    cover = w.cover("cuda")
+    msg = w.message("cuda")
+    stego = torch.empty_like(cover)
+    res = S.new_result()
+    S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res)
+    out = torch.empty(w.msg_bytes, dtype=torch.uint8, device="cuda")
+    res2 = S.new_result()
+    S.stego_extract(stego, out, 0, S.HEADER_BE32, res2)
+    c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+    st, want = O.stream1_embed(c_h, m_h, header=True)
+    assert st == 0
+    got = stego.cpu().numpy()
+    assert np.array_equal(got, want)
+    r = S.read_result(res)
+    assert r["status"] == 0 and (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+    r2 = S.read_result(res2)
+    assert r2["status"] == 0 and r2["msg_bytes"] == w.msg_bytes
+    assert np.array_equal(out.cpu().numpy(), m_h)
+    # in place on a copy gives the same bytes
+    buf = cover.clone()
+    S.stego_embed(buf, buf, msg, S.HEADER_BE32)
+    assert torch.equal(buf, stego)
