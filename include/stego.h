@@ -243,6 +243,26 @@ int stego_extract_batched(const stego_desc *d_descs, uint32_t n, stego_result *d
                           uint32_t flags, const stego_tune *tune, void *d_ws,
                           uint64_t ws_bytes, void *stream);
 
+/* Batched embed that allocates nothing, for callers that cannot call
+ * cudaMalloc (a host program with no device allocator of its own, or one that
+ * may not add cudaMalloc's implicit device synchronisation to a per-request
+ * path).  The paper has no counterpart; it is stego_embed_batched with the
+ * workspace taken from a scratch array inside the library instead of d_ws.
+ *   n  at most STEGO_NOALLOC_MAX_DESCS; larger batches return
+ *      STEGO_E_NOMEM and nothing is launched.
+ * Other arguments, results and per-cover errors as for stego_embed_batched.
+ * The scratch array (about 320 KiB) is one per GPU, held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * sets up that device (it looks up the array's device address with
+ * cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller, e.g. by issuing them on one stream.  Each call
+ * rewrites all the scratch it uses, so no clearing is needed between calls. */
+#define STEGO_NOALLOC_MAX_DESCS 8192u
+int stego_embed_batched_noalloc(const stego_desc *d_descs, uint32_t n, stego_result *d_results,
+                                uint32_t flags, const stego_tune *tune, void *stream);
+
 /* CUDA graph of one batched call.  The descriptors, results and workspace
  * are captured by address: fill the same device arrays with new descriptors
  * (same n) and replay, which re-runs the three launches of the call without

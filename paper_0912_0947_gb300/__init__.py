@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
             f = getattr(L, name)
             f.argtypes = [_vp, _u32, _vp, _u32, ctypes.POINTER(Tune), _vp, _u64, _vp]
             f.restype = _int
+        L.stego_embed_batched_noalloc.argtypes = [_vp, _u32, _vp, _u32, ctypes.POINTER(Tune), _vp]
+        L.stego_embed_batched_noalloc.restype = _int
         L.stego_set_tune.argtypes = [_int, ctypes.POINTER(Tune)]
         L.stego_set_tune.restype = _int
         L.stego_get_tune.argtypes = [_int, ctypes.POINTER(Tune)]
@@ -260,6 +262,22 @@ def stego_extract_batched(descs, n: int, results, flags: int, ws, tune=None, str
                                      ws.numel() * ws.element_size(),
                                      _stream_ptr(stream, descs.device))
     _check(st, "stego_extract_batched")
+
+
+# largest batch stego_embed_batched_noalloc accepts (STEGO_NOALLOC_MAX_DESCS)
+NOALLOC_MAX_DESCS = 8192
+
+
+def stego_embed_batched_noalloc(descs, n: int, results, flags: int, tune=None,
+                                stream=None) -> None:
+    """Batched embed with no workspace argument, for callers that cannot
+    allocate device memory: the library's own per-GPU scratch array stands in
+    for it.  At most NOALLOC_MAX_DESCS covers; calls that overlap on the GPU
+    race on the shared scratch, so issue them on one stream."""
+    st = lib().stego_embed_batched_noalloc(_dev_ptr(descs, "descs", None), int(n),
+                                           _dev_ptr(results, "results", torch.int64), int(flags),
+                                           _tune(tune), _stream_ptr(stream, descs.device))
+    _check(st, "stego_embed_batched_noalloc")
 
 
 def stego_set_tune(op: int, tune) -> None:

@@ -21,6 +21,7 @@
 //   [64, 64 + 8(n+1))       tile offsets (counts before the scan)
 //   [info_off, +32n)        per-descriptor derived sizes and flags
 #include <cstring>
+#include <mutex>
 
 #include "s1_device.cuh"
 
@@ -521,3 +522,69 @@ int stego_graph_destroy(stego_graph *g)
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched embed for callers that cannot allocate device memory
+// ---------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc at all: a host program with no device
+// allocator of its own, or one that may not add cudaMalloc's implicit device
+// synchronisation to its per-request path.  They still own descriptors,
+// covers, messages and results; only the batched call's scratch (tile
+// counter, tile offsets, per-cover sizes) moves into this file-scope array,
+// sized for STEGO_NOALLOC_MAX_DESCS covers.  Every GPU that loads the library
+// holds it until the process exits.
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxDescs = STEGO_NOALLOC_MAX_DESCS;
+constexpr uint64_t kNoAllocBytes =
+    ((64ull + 8ull * (kNoAllocMaxDescs + 1ull) + 15ull) & ~15ull) + 32ull * kNoAllocMaxDescs;
+constexpr int kNoAllocDevices = 64;
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocDevices]; // device address of the array, per device
+
+} // namespace
+
+// In host code this name is only a host-side stand-in for the device array:
+// the kernels get the address that cudaGetSymbolAddress returns.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return STEGO_E_CUDA;
+    if (dev < 0 || dev >= kNoAllocDevices)
+        return STEGO_E_INVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+            return STEGO_E_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return STEGO_OK;
+}
+
+} // namespace
+
+extern "C" int stego_embed_batched_noalloc(const stego_desc *d_descs, uint32_t n,
+                                           stego_result *d_results, uint32_t flags,
+                                           const stego_tune *tune, void *stream)
+{
+    if (n > kNoAllocMaxDescs)
+        return STEGO_E_NOMEM;
+    void *ws = nullptr;
+    const int st = noalloc_scratch(&ws);
+    if (st != STEGO_OK)
+        return st;
+    // the prep and scan launches rewrite every scratch word the persistent
+    // kernel reads, so the previous call's contents need no clearing
+    return stego::batched<true>(d_descs, n, d_results, flags, tune, ws, kNoAllocBytes, stream);
+}
