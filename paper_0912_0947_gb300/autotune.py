@@ -1,0 +1,131 @@
+"""Launch-shape autotuner.
+
+Times candidate launch shapes (threads per CTA, 16-byte vectors in flight
+per thread, resident CTAs per SM, and for batched calls the tile size) of
+one operation on the caller's own buffers with CUDA events, flushing the L2
+between repetitions, and installs the fastest with ``stego_set_tune`` so
+every later call of that operation uses it.  Choices are cached per device
+name, operation and workload size class in a JSON file
+(``$STEGO_TUNE_CACHE`` or ``~/.cache/paper_0912_0947_gb300/tune.json``).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+import torch
+
+from . import Tune, stego_get_tune, stego_set_tune
+
+L2_FLUSH_BYTES = 256 << 20
+
+SINGLE_CANDIDATES = [(t, v, c) for t in (128, 256, 512) for v in (2, 4, 8) for c in (0, 2, 4, 8)]
+BATCHED_CANDIDATES = [(t, v, 0, tile) for t in (256, 512) for v in (2, 4, 8)
+                      for tile in (16384, 65536, 262144, 1 << 20)]
+
+
+def cache_path() -> str:
+    p = os.environ.get("STEGO_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_0912_0947_gb300", "tune.json")
+
+
+def _key(op: int, size_bytes: int, device=None) -> str:
+    name = torch.cuda.get_device_name(device)
+    cls = int(math.log2(max(size_bytes, 1)))
+    return "%s|op%d|2^%d" % (name, op, cls)
+
+
+def load_cached(op: int, size_bytes: int, install: bool = True, device=None):
+    try:
+        with open(cache_path()) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    v = d.get(_key(op, size_bytes, device))
+    if v is None:
+        return None
+    if install:
+        stego_set_tune(op, tuple(v["shape"]))
+    return v
+
+
+def _store(op: int, size_bytes: int, shape, us: float, device=None) -> None:
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        try:
+            with open(p) as f:
+                d = json.load(f)
+        except (OSError, ValueError):
+            d = {}
+        d[_key(op, size_bytes, device)] = {"shape": list(shape), "us": us}
+        tmp = p + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+class Flusher:
+    """Evicts the L2 between timed repetitions: writes a buffer larger than
+    the L2, then reads another one so the written lines are cleaned before
+    the timed call (a dirty L2 would charge its write-back to that call)."""
+
+    def __init__(self, device, nbytes: int = L2_FLUSH_BYTES):
+        self.a = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.b = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+
+    def __call__(self):
+        self.a.fill_(1)
+        self.b.sum(dtype=torch.int32)
+
+
+def time_call(fn, flush, reps: int = 15, stream=None) -> float:
+    """Median event time (microseconds) of fn() after a flush, over reps."""
+    stream = stream or torch.cuda.current_stream()
+    evs = []
+    for _ in range(reps + 2):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ts = [a.elapsed_time(b) * 1e3 for a, b in evs[2:]]
+    return statistics.median(ts)
+
+
+def autotune(op: int, fn, size_bytes: int, candidates=None, flush=None, reps: int = 15,
+             use_cache: bool = True, install: bool = True, device=None):
+    """Pick the fastest launch shape for ``op`` running ``fn()``.
+
+    Returns (best shape tuple, best microseconds, table of (shape, us))."""
+    if use_cache:
+        hit = load_cached(op, size_bytes, install=install, device=device)
+        if hit is not None:
+            return tuple(hit["shape"]), hit["us"], []
+    if candidates is None:
+        candidates = BATCHED_CANDIDATES if op >= 3 else SINGLE_CANDIDATES
+    flush = flush or Flusher(device or torch.cuda.current_device())
+    old = stego_get_tune(op)
+    table = []
+    try:
+        fn()  # first-call work (occupancy queries) outside the timing
+        for shape in candidates:
+            full = tuple(shape) + (0,) * (4 - len(shape))
+            stego_set_tune(op, full)
+            table.append((full, time_call(fn, flush, reps)))
+    finally:
+        stego_set_tune(op, Tune(old.threads, old.vec_per_thread, old.ctas_per_sm, old.tile_bytes))
+    best, us = min(table, key=lambda r: r[1])
+    if install:
+        stego_set_tune(op, best)
+    _store(op, size_bytes, best, us, device)
+    return best, us, table

@@ -16,7 +16,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 Shape g_shape[STEGO_OP_COUNT] = {
     {256, 4, 0, 0},      // embed
-    {256, 4, 0, 0},      // extract
+    {256, 8, 0, 0},      // extract
     {256, 4, 0, 0},      // changed
     {256, 4, 0, 65536},  // embed batched
     {256, 4, 0, 65536},  // extract batched

@@ -78,9 +78,18 @@ __device__ __forceinline__ uint32_t spread_lo(uint32_t rep)
     return (((rep & 0x01020408u) + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
 }
 
+// Changed bytes of one embedded word.  Only bit 0 of a byte can differ
+// between cover and stego in this layout, so (stego ^ cover) has at most the
+// four bits 0, 8, 16, 24 set and its population count is the number of
+// changed bytes.  Each changed byte moves by exactly one, so the same count
+// is also the word's squared error.
+__device__ __forceinline__ uint32_t lsb_changes(uint32_t o, uint32_t c) { return __popc(o ^ c); }
+
 // 16-byte vectors v = v_first + i*step (+ u*blockDim.x for u < V), v < v_end,
 // of a job whose cover and stego are 16-byte aligned.  Each warp's 128-bit
-// load and store instructions cover 512 contiguous bytes.
+// load and store instructions cover 512 contiguous bytes.  With STATS the
+// changed-byte count (= squared error, see lsb_changes) is added to both
+// accumulators.
 template <int V, bool STATS>
 __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_first,
                                                 uint64_t v_end, uint64_t step,
@@ -105,6 +114,7 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
             if (v < v_end && (v << 4) < a.t_bytes)
                 p[u] = stream_pair(a, v << 1);
         }
+        uint32_t n = 0;
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const uint64_t v = v0 + (uint64_t)u * blockDim.x;
@@ -116,19 +126,21 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
                 const uint32_t r0 = __byte_perm(p[u], 0u, 0x0000u);
                 o.x = (c[u].x & 0xFEFEFEFEu) | spread_hi(r0);
                 o.y = (c[u].y & 0xFEFEFEFEu) | spread_lo(r0);
+                if (STATS)
+                    n += lsb_changes(o.x, c[u].x) + lsb_changes(o.y, c[u].y);
                 if (k0 + 8 < a.t_bytes) { // T is a multiple of 8
                     const uint32_t r1 = __byte_perm(p[u], 0u, 0x1111u);
                     o.z = (c[u].z & 0xFEFEFEFEu) | spread_hi(r1);
                     o.w = (c[u].w & 0xFEFEFEFEu) | spread_lo(r1);
+                    if (STATS)
+                        n += lsb_changes(o.z, c[u].z) + lsb_changes(o.w, c[u].w);
                 }
             }
             __stcs(dst + v, o);
-            if (STATS) {
-                word_stats(o.x, c[u].x, changed, sse);
-                word_stats(o.y, c[u].y, changed, sse);
-                word_stats(o.z, c[u].z, changed, sse);
-                word_stats(o.w, c[u].w, changed, sse);
-            }
+        }
+        if (STATS) {
+            changed += n;
+            sse += n;
         }
     }
 }
