@@ -278,6 +278,115 @@ int stego_graph_capture_batched(int op, const stego_desc *d_descs, uint32_t n,
 int stego_graph_launch(stego_graph *g, void *stream);
 int stego_graph_destroy(stego_graph *g);
 
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of embed / extract requests            */
+/* ------------------------------------------------------------------ */
+/* A server owns one dispatcher thread and `slots` CUDA streams.  Requests
+ * of mixed sizes are queued by stego_server_submit (any thread).  Whenever a
+ * slot is free the dispatcher admits queued requests in arrival order while
+ * the sum of their working-set bytes (embed: 2*cover_bytes + msg_bytes;
+ * extract: cover_bytes + msg_bytes) stays within budget_bytes, up to
+ * max_batch requests, and launches them as one stego_embed_batched plus one
+ * stego_extract_batched on that slot's stream.  Requests arriving while
+ * batches run are admitted into the next free slot as soon as budget frees
+ * up, so batches overlap on the device.  A request whose own bytes exceed
+ * the budget completes at once with STEGO_E_NOMEM; an unknown op with
+ * STEGO_E_INVAL.  This is the paper's per-row / per-frame call repeated
+ * (Section VI, last paragraph) turned into a request stream.
+ * Buffers named in requests are caller-owned, device-accessible, and must
+ * stay valid until the request's completion has been returned. */
+typedef struct stego_server stego_server;
+
+typedef struct stego_server_config {
+    uint32_t slots;        /* batches in flight at once (1..16)             */
+    uint32_t max_batch;    /* requests per batch (1..8192)                  */
+    uint64_t budget_bytes; /* in-flight working-set budget, bytes           */
+    stego_tune tune_embed; /* launch shapes of the batched calls (zeros =   */
+    stego_tune tune_extract; /*  the installed choice)                      */
+} stego_server_config;     /* 48 bytes */
+
+typedef struct stego_request {
+    uint32_t op;           /* STEGO_OP_EMBED or STEGO_OP_EXTRACT            */
+    uint32_t flags;        /* STEGO_LAYOUT_STREAM1 [| STEGO_HEADER_BE32]    */
+    const uint8_t *cover;  /* embed: cover; extract: stego image            */
+    uint8_t *stego;        /* embed: output image                           */
+    uint8_t *msg;          /* embed: message (read); extract: output buffer */
+    uint64_t cover_bytes;
+    uint64_t msg_bytes;    /* embed: length; extract: capacity of msg       */
+    uint64_t msg_len;      /* extract without a header: bytes to extract    */
+    uint64_t tag;          /* returned in the completion                    */
+} stego_request;           /* 64 bytes */
+
+typedef struct stego_completion {
+    uint64_t tag;
+    uint64_t changed;      /* embed: changed bytes (stats always fused)     */
+    uint64_t sse;          /* embed: squared error                          */
+    uint64_t msg_bytes;    /* embedded / extracted message bytes            */
+    int32_t status;        /* STEGO_OK or the request's error               */
+    int32_t batch_size;    /* requests in the batch that carried it         */
+    double t_submit;       /* server clock, seconds: queued (open loop: the */
+    double t_dispatch;     /*   scheduled arrival), launched, and seen done */
+    double t_done;
+} stego_completion;        /* 64 bytes */
+
+/* Device arena (bytes) a server with this configuration needs: per slot its
+ * descriptors, results and batched workspaces.  0 for an invalid config. */
+uint64_t stego_server_arena_bytes(const stego_server_config *cfg);
+
+/* Creates a server on the current device.  d_arena: caller-owned device
+ * memory of arena_bytes >= stego_server_arena_bytes(cfg), 256-byte aligned,
+ * used until stego_server_destroy.  The server allocates no device memory;
+ * it allocates its pinned host staging (descriptors and results) here. */
+int stego_server_create(const stego_server_config *cfg, void *d_arena, uint64_t arena_bytes,
+                        stego_server **out);
+
+/* Queues n requests (copied); thread-safe. */
+int stego_server_submit(stego_server *s, const stego_request *reqs, uint32_t n);
+
+/* Moves up to max finished completions into out; *n_out = how many. */
+int stego_server_poll(stego_server *s, stego_completion *out, uint32_t max, uint32_t *n_out);
+
+/* Waits until every submitted request has completed (their completions stay
+ * queued for stego_server_poll); STEGO_E_TIMEOUT after timeout_s seconds. */
+int stego_server_drain(stego_server *s, double timeout_s);
+
+/* Open-loop load: the calling thread submits reqs[i] at arrival_s[i]
+ * seconds after the call starts (server clock), then waits for all of them
+ * (at most timeout_s) and writes completion i to out[i] (tags are set to i;
+ * latency counts from the scheduled arrival).  The server must be idle. */
+int stego_server_run_open_loop(stego_server *s, const stego_request *reqs,
+                               const double *arrival_s, uint32_t n, stego_completion *out,
+                               double timeout_s);
+
+/* Seconds since the server was created; batches launched, requests
+ * outstanding and the largest in-flight working set admitted so far (any
+ * out pointer may be NULL). */
+double stego_server_clock(stego_server *s);
+int stego_server_stats(stego_server *s, uint64_t *batches, uint64_t *outstanding,
+                       uint64_t *peak_in_flight_bytes);
+
+/* Finishes queued and in-flight work, stops the dispatcher, frees the
+ * server (not the arena). */
+int stego_server_destroy(stego_server *s);
+
+/* Where a buffer lives, as the CUDA runtime of the current device reports
+ * it, and whether this library's kernels may read and write it directly.
+ *   *kind: STEGO_MEM_PAGEABLE (ordinary host memory), STEGO_MEM_PINNED
+ *          (page-locked host memory), STEGO_MEM_DEVICE, STEGO_MEM_MANAGED.
+ *   *device_accessible: 1 when a kernel may dereference p itself: device
+ *          and managed memory, pinned host memory mapped at the same address
+ *          (the usual case with unified addressing; the kernel then reads
+ *          and writes host memory over the CPU-GPU link), and pageable host
+ *          memory only when the device reports pageable-memory access.
+ * Every entry point accepts device-accessible pointers of any kind; this
+ * call lets a caller check a host buffer before passing it.
+ * Returns STEGO_OK or STEGO_E_CUDA. */
+#define STEGO_MEM_PAGEABLE 0
+#define STEGO_MEM_PINNED 1
+#define STEGO_MEM_DEVICE 2
+#define STEGO_MEM_MANAGED 3
+int stego_pointer_kind(const void *p, int *kind, int *device_accessible);
+
 /* Install / read the launch shape used by an operation (enum stego_op) on
  * every device.  Zero fields of `t` keep their built-in defaults.
  * Returns STEGO_E_INVAL for an unknown op or an out-of-range field. */

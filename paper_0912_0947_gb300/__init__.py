@@ -64,6 +64,24 @@ class Tune(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("tile_bytes", ctypes.c_uint32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("budget_bytes", ctypes.c_uint64), ("tune_embed", Tune),
+                ("tune_extract", Tune)]
+
+
+# stego_request / stego_completion as laid out in host memory (64 bytes each)
+REQUEST_DTYPE = np.dtype([
+    ("op", "<u4"), ("flags", "<u4"), ("cover", "<u8"), ("stego", "<u8"), ("msg", "<u8"),
+    ("cover_bytes", "<u8"), ("msg_bytes", "<u8"), ("msg_len", "<u8"), ("tag", "<u8"),
+])
+COMPLETION_DTYPE = np.dtype([
+    ("tag", "<u8"), ("changed", "<u8"), ("sse", "<u8"), ("msg_bytes", "<u8"),
+    ("status", "<i4"), ("batch_size", "<i4"),
+    ("t_submit", "<f8"), ("t_dispatch", "<f8"), ("t_done", "<f8"),
+])
+assert REQUEST_DTYPE.itemsize == 64 and COMPLETION_DTYPE.itemsize == 64
+
 _LIB = None
 _vp = ctypes.c_void_p
 _u64 = ctypes.c_uint64
@@ -103,6 +121,28 @@ def lib() -> ctypes.CDLL:
             f.restype = _int
         L.stego_embed_batched_noalloc.argtypes = [_vp, _u32, _vp, _u32, ctypes.POINTER(Tune), _vp]
         L.stego_embed_batched_noalloc.restype = _int
+        L.stego_pointer_kind.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]
+        L.stego_pointer_kind.restype = _int
+        L.stego_server_arena_bytes.argtypes = [ctypes.POINTER(ServerConfig)]
+        L.stego_server_arena_bytes.restype = _u64
+        L.stego_server_create.argtypes = [ctypes.POINTER(ServerConfig), _vp, _u64,
+                                          ctypes.POINTER(_vp)]
+        L.stego_server_create.restype = _int
+        L.stego_server_submit.argtypes = [_vp, _vp, _u32]
+        L.stego_server_submit.restype = _int
+        L.stego_server_poll.argtypes = [_vp, _vp, _u32, ctypes.POINTER(_u32)]
+        L.stego_server_poll.restype = _int
+        L.stego_server_drain.argtypes = [_vp, ctypes.c_double]
+        L.stego_server_drain.restype = _int
+        L.stego_server_run_open_loop.argtypes = [_vp, _vp, _vp, _u32, _vp, ctypes.c_double]
+        L.stego_server_run_open_loop.restype = _int
+        L.stego_server_clock.argtypes = [_vp]
+        L.stego_server_clock.restype = ctypes.c_double
+        L.stego_server_stats.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                         ctypes.POINTER(_u64)]
+        L.stego_server_stats.restype = _int
+        L.stego_server_destroy.argtypes = [_vp]
+        L.stego_server_destroy.restype = _int
         L.stego_set_tune.argtypes = [_int, ctypes.POINTER(Tune)]
         L.stego_set_tune.restype = _int
         L.stego_get_tune.argtypes = [_int, ctypes.POINTER(Tune)]
@@ -134,13 +174,20 @@ def _check(st: int, where: str) -> int:
 # -- marshalling helpers -------------------------------------------------------
 
 def _dev_ptr(t, what: str, dtype=torch.uint8):
-    """Device address of a contiguous CUDA tensor (or None)."""
+    """Address of a contiguous tensor the kernels can dereference (or None):
+    CUDA memory, or pinned host memory mapped into the device's address space
+    (the kernels then read and write it over the CPU-GPU link; no copy).
+    Pageable CPU tensors are refused: there is no CPU fallback."""
     if t is None:
         return None
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch.Tensor" % what)
     if t.device.type != "cuda":
-        raise ValueError("%s must live on a CUDA device (no CPU fallback)" % what)
+        if not (t.device.type == "cpu" and t.is_pinned()):
+            raise ValueError("%s must live on a CUDA device or in pinned host memory "
+                             "(no CPU fallback)" % what)
+        if t.numel() > 0 and not stego_pointer_kind(t.data_ptr())[1]:
+            raise ValueError("%s: pinned host memory not mapped for the device" % what)
     if dtype is not None and t.dtype != dtype:
         raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
     if not t.is_contiguous():
@@ -150,6 +197,8 @@ def _dev_ptr(t, what: str, dtype=torch.uint8):
 
 def _stream_ptr(stream, device=None):
     if stream is None:
+        if device is not None and torch.device(device).type != "cuda":
+            device = None  # host (zero-copy) buffers: the current CUDA device
         stream = torch.cuda.current_stream(device)
     if isinstance(stream, int):
         return stream or None
@@ -280,6 +329,17 @@ def stego_embed_batched_noalloc(descs, n: int, results, flags: int, tune=None,
     _check(st, "stego_embed_batched_noalloc")
 
 
+MEM_PAGEABLE, MEM_PINNED, MEM_DEVICE, MEM_MANAGED = range(4)
+
+
+def stego_pointer_kind(ptr: int):
+    """(kind, device_accessible) of an address (see include/stego.h)."""
+    k, a = _int(0), _int(0)
+    _check(lib().stego_pointer_kind(_vp(ptr), ctypes.byref(k), ctypes.byref(a)),
+           "stego_pointer_kind")
+    return k.value, bool(a.value)
+
+
 def stego_set_tune(op: int, tune) -> None:
     t = tune if isinstance(tune, Tune) else Tune(*[int(x) for x in tune])
     _check(lib().stego_set_tune(int(op), ctypes.byref(t)), "stego_set_tune")
@@ -338,3 +398,81 @@ def pack_descs(items) -> np.ndarray:
 def descs_to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
     t = torch.from_numpy(a.view(np.uint8).copy())
     return t.to(device)
+
+
+# -- serving ---------------------------------------------------------------------
+
+class Server:
+    """A stego_server: continuous batching of embed / extract requests
+    (include/stego.h).  The device arena is a torch tensor owned here."""
+
+    def __init__(self, slots: int = 4, max_batch: int = 256, budget_bytes: int = 40 << 30,
+                 tune_embed=(0, 0, 0, 0), tune_extract=(0, 0, 0, 0), device="cuda"):
+        cfg = ServerConfig(int(slots), int(max_batch), int(budget_bytes),
+                           Tune(*tune_embed), Tune(*tune_extract))
+        n = int(lib().stego_server_arena_bytes(ctypes.byref(cfg)))
+        if n == 0:
+            raise StegoError(E_INVAL, "stego_server_arena_bytes")
+        self.arena = torch.empty(n, dtype=torch.uint8, device=device)
+        h = _vp(0)
+        _check(lib().stego_server_create(ctypes.byref(cfg), self.arena.data_ptr(), n,
+                                         ctypes.byref(h)), "stego_server_create")
+        self._h = h
+        self.cfg = cfg
+
+    @staticmethod
+    def requests(items) -> np.ndarray:
+        """Pack dicts (keys of REQUEST_DTYPE; tensors allowed for cover,
+        stego, msg) into a host array of stego_request records."""
+        a = np.zeros(len(items), dtype=REQUEST_DTYPE)
+        for i, it in enumerate(items):
+            for k, v in it.items():
+                if isinstance(v, torch.Tensor):
+                    v = _dev_ptr(v, k) or 0
+                a[i][k] = v
+        return a
+
+    def submit(self, reqs: np.ndarray) -> None:
+        reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+        _check(lib().stego_server_submit(self._h, reqs.ctypes.data, len(reqs)),
+               "stego_server_submit")
+
+    def poll(self, max_n: int = 4096) -> np.ndarray:
+        out = np.zeros(max_n, dtype=COMPLETION_DTYPE)
+        k = _u32(0)
+        _check(lib().stego_server_poll(self._h, out.ctypes.data, max_n, ctypes.byref(k)),
+               "stego_server_poll")
+        return out[: k.value]
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(lib().stego_server_drain(self._h, float(timeout_s)), "stego_server_drain")
+
+    def run_open_loop(self, reqs: np.ndarray, arrival_s: np.ndarray,
+                      timeout_s: float = 120.0) -> np.ndarray:
+        reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        out = np.zeros(len(reqs), dtype=COMPLETION_DTYPE)
+        _check(lib().stego_server_run_open_loop(self._h, reqs.ctypes.data, arr.ctypes.data,
+                                                len(reqs), out.ctypes.data, float(timeout_s)),
+               "stego_server_run_open_loop")
+        return out
+
+    def clock(self) -> float:
+        return float(lib().stego_server_clock(self._h))
+
+    def stats(self) -> dict:
+        b, o, p = _u64(0), _u64(0), _u64(0)
+        _check(lib().stego_server_stats(self._h, ctypes.byref(b), ctypes.byref(o),
+                                        ctypes.byref(p)), "stego_server_stats")
+        return {"batches": b.value, "outstanding": o.value, "peak_in_flight_bytes": p.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().stego_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

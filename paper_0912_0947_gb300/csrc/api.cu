@@ -15,8 +15,8 @@ constexpr int kMaxDevices = 64;
 
 std::mutex g_mu;
 Shape g_shape[STEGO_OP_COUNT] = {
-    {256, 4, 0, 0},      // embed
-    {256, 8, 0, 0},      // extract
+    {512, 4, 0, 0},      // embed
+    {128, 4, 0, 0},      // extract
     {256, 4, 0, 0},      // changed
     {256, 4, 0, 65536},  // embed batched
     {256, 4, 0, 65536},  // extract batched
@@ -337,6 +337,44 @@ int stego_changed_bytes(const uint8_t *d_a, const uint8_t *d_b, uint64_t n, uint
     return cuda_status(changed_bytes(d_a, d_b, n, reinterpret_cast<unsigned long long *>(d_out2), sh, s));
 }
 
+int stego_pointer_kind(const void *p, int *kind, int *device_accessible)
+{
+    if (!kind || !device_accessible)
+        return STEGO_E_INVAL;
+    *kind = STEGO_MEM_PAGEABLE;
+    *device_accessible = 0;
+    cudaPointerAttributes at;
+    std::memset(&at, 0, sizeof(at));
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return STEGO_E_CUDA;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeDevice:
+        *kind = STEGO_MEM_DEVICE;
+        *device_accessible = 1;
+        break;
+    case cudaMemoryTypeManaged:
+        *kind = STEGO_MEM_MANAGED;
+        *device_accessible = 1;
+        break;
+    case cudaMemoryTypeHost:
+        *kind = STEGO_MEM_PINNED;
+        *device_accessible = at.devicePointer == p ? 1 : 0;
+        break;
+    default: {
+        int dev = 0, pageable = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess)
+            pageable = 0;
+        *kind = STEGO_MEM_PAGEABLE;
+        *device_accessible = pageable ? 1 : 0;
+        break;
+    }
+    }
+    return STEGO_OK;
+}
+
 int stego_set_tune(int op, const stego_tune *t)
 {
     if (op < 0 || op >= STEGO_OP_COUNT || !t || !valid_tune_field_ranges(*t))
@@ -372,3 +410,6 @@ static_assert(sizeof(stego_desc) == 72, "stego_desc layout");
 static_assert(sizeof(stego_result) == 32, "stego_result layout");
 static_assert(sizeof(stego_geom) == 16, "stego_geom layout");
 static_assert(sizeof(stego_tune) == 16, "stego_tune layout");
+static_assert(sizeof(stego_request) == 64, "stego_request layout");
+static_assert(sizeof(stego_completion) == 64, "stego_completion layout");
+static_assert(sizeof(stego_server_config) == 48, "stego_server_config layout");

@@ -1,0 +1,159 @@
+"""The continuous-batching server: every request's result is the same alone
+and in the mix (bit for bit, tolerance 0), admission never exceeds the
+budget, and bad requests complete with an error instead of hanging."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import need_gpu
+from paper_0912_0947_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    return need_gpu()
+
+
+class Pool:
+    """Covers of uneven sizes resident on the device, their pre-embedded
+    stegos, and one distinct output slot per request."""
+
+    def __init__(self, S, rng, n_covers, n_req, embed_frac=0.7):
+        items = synth.uneven_batch(n_covers, seed=int(rng.integers(1 << 30)), lo=16, hi=700)
+        self.sizes = [it.cover_bytes for it in items]
+        self.mlen = [it.msg_bytes for it in items]
+        self.covers = [torch.from_numpy(rng.integers(0, 256, c, dtype=np.uint8)).cuda()
+                       for c in self.sizes]
+        self.msgs = [torch.from_numpy(rng.integers(0, 256, m, dtype=np.uint8)).cuda()
+                     for m in self.mlen]
+        self.stegos = []
+        for c, m in zip(self.covers, self.msgs):
+            s = torch.empty_like(c)
+            S.stego_embed(c, s, m, S.HEADER_BE32)
+            self.stegos.append(s)
+        self.ops = (rng.random(n_req) >= embed_frac).astype(int)  # 0 embed, 1 extract
+        self.ids = rng.integers(0, n_covers, n_req)
+        self.out = []
+        recs = []
+        for r in range(n_req):
+            i = int(self.ids[r])
+            if self.ops[r] == 0:
+                o = torch.full((self.sizes[i],), 0x5A, dtype=torch.uint8, device="cuda")
+                recs.append(dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=self.covers[i],
+                                 stego=o, msg=self.msgs[i], cover_bytes=self.sizes[i],
+                                 msg_bytes=self.mlen[i]))
+            else:
+                o = torch.full((self.mlen[i] + 3,), 0xEE, dtype=torch.uint8, device="cuda")
+                recs.append(dict(op=S.OP_EXTRACT, flags=S.HEADER_BE32, cover=self.stegos[i],
+                                 msg=o, cover_bytes=self.sizes[i], msg_bytes=self.mlen[i] + 3))
+            self.out.append(o)
+        self.reqs = S.Server.requests(recs)
+        for r in range(n_req):
+            self.reqs[r]["tag"] = r
+
+    def reset_outputs(self):
+        for r, o in enumerate(self.out):
+            o.fill_(0x5A if self.ops[r] == 0 else 0xEE)
+
+    def snapshot(self):
+        torch.cuda.synchronize()
+        return [o.clone() for o in self.out]
+
+
+def _by_tag(comps):
+    return {int(c["tag"]): c for c in comps}
+
+
+def test_alone_equals_mix(S):
+    rng = np.random.default_rng(31)
+    n_req = 400
+    pool = Pool(S, rng, 48, n_req)
+    # alone: one request at a time on a one-slot, batch-of-one server
+    srv = S.Server(slots=1, max_batch=1, budget_bytes=1 << 34)
+    alone = []
+    for r in range(n_req):
+        srv.submit(pool.reqs[r:r + 1])
+        srv.drain(30)
+        alone.extend(srv.poll())
+    srv.close()
+    a_out = pool.snapshot()
+    a = _by_tag(alone)
+    assert len(a) == n_req and all(c["batch_size"] == 1 for c in alone)
+    # mix: open-loop Poisson arrivals, four slots, batches of up to 64
+    pool.reset_outputs()
+    srv = S.Server(slots=4, max_batch=64, budget_bytes=1 << 34)
+    arrivals = synth.poisson_arrivals(50000.0, n_req, 77)
+    comps = srv.run_open_loop(pool.reqs, arrivals, timeout_s=60)
+    st = srv.stats()
+    srv.close()
+    m = _by_tag(comps)
+    assert sorted(m) == list(range(n_req))
+    for r in range(n_req):
+        for k in ("status", "changed", "sse", "msg_bytes"):
+            assert int(m[r][k]) == int(a[r][k]), (r, k)
+        assert int(m[r]["status"]) == 0
+    m_out = pool.snapshot()
+    for r in range(n_req):
+        assert torch.equal(m_out[r], a_out[r]), r
+    # the mix really batched and overlapped
+    assert max(int(c["batch_size"]) for c in comps) > 1
+    assert st["batches"] < n_req
+    # a sample against the oracle
+    O = oracle.load()
+    for r in range(0, n_req, 37):
+        i = int(pool.ids[r])
+        c = pool.covers[i].cpu().numpy()
+        msg = pool.msgs[i].cpu().numpy()
+        stt, want = O.stream1_embed(c, msg, header=True)
+        if pool.ops[r] == 0:
+            assert np.array_equal(m_out[r].cpu().numpy(), want)
+            assert (int(m[r]["changed"]), int(m[r]["sse"])) == O.changed_bytes(c, want)
+        else:
+            assert np.array_equal(m_out[r].cpu().numpy()[: msg.size], msg)
+
+
+def test_budget_and_bad_requests(S):
+    rng = np.random.default_rng(32)
+    C = 1 << 20
+    covers = [torch.from_numpy(rng.integers(0, 256, C, dtype=np.uint8)).cuda() for _ in range(6)]
+    msg = torch.from_numpy(rng.integers(0, 256, 1000, dtype=np.uint8)).cuda()
+    outs = [torch.empty(C, dtype=torch.uint8, device="cuda") for _ in range(6)]
+    recs = [dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=covers[i], stego=outs[i], msg=msg,
+                 cover_bytes=C, msg_bytes=1000, tag=i) for i in range(6)]
+    big = torch.empty(8 * C, dtype=torch.uint8, device="cuda")
+    recs.append(dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=big, stego=big, msg=msg,
+                     cover_bytes=8 * C, msg_bytes=1000, tag=100))          # over the budget
+    recs.append(dict(op=99, cover=covers[0], cover_bytes=C, tag=101))       # unknown op
+    recs.append(dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=covers[1], stego=outs[1], msg=msg,
+                     cover_bytes=C, msg_bytes=C // 8, tag=102))            # too long a message
+    budget = 5 * C  # two embeds of 2C + 1000 fit, a third does not
+    srv = S.Server(slots=3, max_batch=8, budget_bytes=budget)
+    srv.submit(S.Server.requests(recs))
+    srv.drain(30)
+    comps = _by_tag(srv.poll())
+    st = srv.stats()
+    srv.close()
+    assert sorted(comps) == list(range(6)) + [100, 101, 102]
+    for i in range(6):
+        assert int(comps[i]["status"]) == 0
+    assert int(comps[100]["status"]) == S.E_NOMEM
+    assert int(comps[101]["status"]) == S.E_INVAL
+    assert int(comps[102]["status"]) == S.E_CAPACITY
+    assert 0 < st["peak_in_flight_bytes"] <= budget
+    assert st["outstanding"] == 0
+    torch.cuda.synchronize()
+    ref = torch.empty(C, dtype=torch.uint8, device="cuda")
+    S.stego_embed(covers[3], ref, msg, S.HEADER_BE32)
+    assert torch.equal(ref, outs[3])
+
+
+def test_server_config_errors(S):
+    for cfg in (dict(slots=0), dict(slots=17), dict(max_batch=0), dict(max_batch=9000),
+                dict(budget_bytes=0)):
+        kw = dict(slots=2, max_batch=8, budget_bytes=1 << 20)
+        kw.update(cfg)
+        with pytest.raises(S.StegoError):
+            S.Server(**kw)
