@@ -199,19 +199,30 @@ def run_ours(args, rank, world, local_rank):
     stats = S.read_result(res_e)
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
-    if rank == 0 or world > 1:
+    if (rank == 0 or world > 1) and args.e2e_steps > 0:
         e2e = run_e2e_zero_copy(args, S, torch, dev, stream, cover, msg, C, m)
         e2e["explicit_copy"] = run_e2e(args, S, torch, dev, stream, cover, msg, C, m)
     # ---- batched vs one launch per image -----------------------------------------
     legs = {}
-    if rank == 0 and not args.no_batched:
-        del flush
+    want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
+                                                         "paper2", "serving"}
+    if args.no_batched:
+        want -= {"batched_uneven", "batched_video", "paper2"}
+    if args.no_serving:
+        want.discard("serving")
+    del flush
+    torch.cuda.empty_cache()
+    for kind in ("uneven", "video"):
+        if rank == 0 and "batched_" + kind in want:
+            legs["batched_" + kind] = run_batched_leg(
+                S, AT, torch, dev, stream, synth, kind,
+                count=(args.uneven_count if kind == "uneven" else args.video_frames) or None,
+                tune=not args.no_tune)
+            torch.cuda.empty_cache()
+    if rank == 0 and "paper2" in want:
+        legs["paper2"] = run_paper2_leg(S, AT, torch, dev, synth)
         torch.cuda.empty_cache()
-        legs["batched_uneven"] = run_batched_leg(S, AT, torch, dev, stream, synth, "uneven")
-        torch.cuda.empty_cache()
-        legs["batched_video"] = run_batched_leg(S, AT, torch, dev, stream, synth, "video")
-        torch.cuda.empty_cache()
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and "serving" in want:
         legs["serving"] = run_serving_leg(S, AT, torch, dev, synth,
                                           [1000, 2000, 5000, 10000, 20000, 50000])
         torch.cuda.empty_cache()
@@ -274,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-def run_batched_leg(S, AT, torch, dev, stream, synth, kind):
+def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=True):
     """Many covers in one batched launch (and its CUDA-graph replay) against
     one stego_embed / stego_extract launch per cover, same bytes, same GPU.
 
@@ -283,11 +294,11 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind):
     video:  600 frames of 1920x1080x3, gradient plus noise, one message
             stream split across frames at half capacity, header per frame."""
     if kind == "uneven":
-        items = synth.uneven_batch(4096)
+        items = synth.uneven_batch(count or 4096)
         sizes = [it.cover_bytes for it in items]
         mlens = [it.msg_bytes for it in items]
     else:
-        v = synth.Video()
+        v = synth.Video(frames=count or 600)
         sizes = [v.frame_bytes] * v.frames
         mlens = [v.per_frame_msg] * v.frames
     n = len(sizes)
@@ -350,11 +361,12 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind):
         for i in range(n):
             S.stego_extract(s1[i], o1[i], 0, hdr, res_x1[i], stream=stream)
 
-    tune = {}
+    tune_sel = {}
     for name, op, fn in (("embed", S.OP_EMBED_BATCHED, b_embed),
                          ("extract", S.OP_EXTRACT_BATCHED, b_extract)):
-        best, us, table = AT.autotune(op, fn, p, flush=flush, reps=5, use_cache=False)
-        tune[name] = list(best)
+        if tune:
+            best, us, table = AT.autotune(op, fn, p, flush=flush, reps=5, use_cache=False)
+            tune_sel[name] = list(best)
     t_be = AT.time_call(b_embed, flush, 7)
     t_bx = AT.time_call(b_extract, flush, 7)
     t_1e = AT.time_call(one_embed, flush, 3)
@@ -390,7 +402,7 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind):
                                          "extract": round(t_1x / t_bx, 2)},
         "hbm_frac_batched": {"embed": round(emb_bytes / (t_be * 1e-6) / 1e9 / peak, 4),
                              "extract": round(ext_bytes / (t_bx * 1e-6) / 1e9 / peak, 4)},
-        "launch": tune,
+        "launch": tune_sel,
         "outputs_identical": same,
     }
 
@@ -477,6 +489,56 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds
                         "covers and stegos, 40 GB in-flight budget, 8 slots, batches <= 512",
             "rates": results, "batches": stats["batches"],
             "peak_in_flight_bytes": stats["peak_in_flight_bytes"]}
+
+
+def run_paper2_leg(S, AT, torch, dev, synth):
+    """The paper's own layout (Sections VI/VII) on the 8192x8192x3 cover:
+    plane 0, two bits per byte, floor(W/4)*H = 16,777,216 message bytes (full
+    capacity).  Algorithmic bytes: out of place 2C + N; in place 2*4N + N
+    (carrying plane bytes); extract 4N + N.  The plane bytes are every third
+    byte, so DRAM moves whole 32-byte sectors: in place and extract touch
+    every sector of the cover (about 2C + N and C + N)."""
+    W = H = 8192
+    C, N = W * H * 3, (W // 4) * H
+    cover = synth.uniform_bytes(C, synth.substream(synth.SEED_BASE + 6, 1), dev)
+    msg = synth.uniform_bytes(N, synth.substream(synth.SEED_BASE + 6, 2), dev)
+    stego = torch.empty_like(cover)
+    buf = torch.empty_like(cover)
+    out = torch.empty(N, dtype=torch.uint8, device=dev)
+    res = S.new_result(dev)
+    geom = (W, H, 3, 0)
+    flush = AT.Flusher(dev)
+    fl = S.LAYOUT_PAPER2 | S.FUSE_STATS
+
+    def oop():
+        S.stego_embed(cover, stego, msg, fl, res, geom=geom)
+
+    def inplace():
+        S.stego_embed(buf, buf, msg, fl, res, geom=geom)
+
+    def ext():
+        S.stego_extract(stego, out, N, S.LAYOUT_PAPER2, res, geom=geom)
+
+    t_o = AT.time_call(oop, flush, 15)
+    buf.copy_(cover)
+    t_i = AT.time_call(inplace, flush, 15)
+    t_x = AT.time_call(ext, flush, 15)
+    torch.cuda.synchronize()
+    assert torch.equal(out, msg) and torch.equal(buf, stego)
+    peak, _ = hbm_peak()
+    g = lambda b, us: round(b / (us * 1e-6) / 1e9, 1)
+    return {
+        "workload": "8192x8192x3 cover, plane 0, 2 bits/byte, 16777216-byte message (full capacity)",
+        "embed_out_of_place_us": round(t_o, 2), "embed_in_place_us": round(t_i, 2),
+        "extract_us": round(t_x, 2),
+        "cover_gbs": {"embed_out_of_place": g(C, t_o), "embed_in_place": g(C, t_i),
+                      "extract": g(C, t_x)},
+        "hbm_frac": {"embed_out_of_place": round(g(2 * C + N, t_o) / peak, 4),
+                     "embed_in_place_sectors": round(g(2 * C + N, t_i) / peak, 4),
+                     "extract_sectors": round(g(C + N, t_x) / peak, 4)},
+        "algorithmic_bytes": {"embed_out_of_place": 2 * C + N, "embed_in_place": 9 * N,
+                              "extract": 5 * N},
+    }
 
 
 def tune_dict(t):
@@ -654,6 +716,13 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--uneven-count", type=int, default=0,
+                    help="covers in the uneven batched leg (default 4096)")
+    ap.add_argument("--video-frames", type=int, default=0,
+                    help="frames in the video batched leg (default 600)")
+    ap.add_argument("--legs", default="",
+                    help="comma list of extra legs: batched_uneven,batched_video,paper2,serving "
+                         "(default all)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

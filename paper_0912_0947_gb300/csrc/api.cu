@@ -251,7 +251,11 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
         return cuda_status(s1_embed(d_cover, d_stego, n, T, d_msg, slen, header,
                                     (uint32_t)(8u * msg_bytes), stats, d_result, msg_bytes, sh, s));
     }
-    // PAPER2: copy the cover (out of place), then write the 4N carrying bytes
+    // PAPER2 out of place: one fused pass when the layout allows it
+    if (!inplace && cover_bytes > 0 && p2_fused_ok(d_cover, d_stego, *geom))
+        return cuda_status(p2_embed_fused(d_cover, d_stego, *geom, d_msg, msg_bytes, stats,
+                                          d_result, sh, s));
+    // otherwise copy the cover (out of place), then write the 4N carrying bytes
     if (!inplace && cover_bytes > 0) {
         cudaError_t e = s1_embed(d_cover, d_stego, cover_bytes, 0, nullptr, 0, false, 0, false,
                                  msg_bytes == 0 ? d_result : nullptr, 0, sh, s);

@@ -65,6 +65,14 @@ cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
 cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uint64_t N,
                        stego_result *res, const Shape &sh, cudaStream_t s);
 
+// PAPER2 out of place in one pass (copy and embed fused); usable when
+// p2_fused_ok: distinct 16-byte aligned buffers, 1, 3 or 4 channels and
+// 16-byte aligned rows.  N may be 0 (a copy).
+bool p2_fused_ok(const uint8_t *cover, const uint8_t *stego, const stego_geom &g);
+cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
+                           const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
+                           const Shape &sh, cudaStream_t s);
+
 // Changed-byte count and SSE of two arrays into out2[0..1] (zeroed by the
 // caller).
 cudaError_t changed_bytes(const uint8_t *a, const uint8_t *b, uint64_t n,

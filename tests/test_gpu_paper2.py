@@ -69,7 +69,10 @@ def test_golden(S, O):
 
 
 @pytest.mark.parametrize("W,H,Cch", [(4, 1, 1), (5, 3, 1), (9, 4, 3), (33, 7, 3), (64, 16, 4),
-                                     (1024, 1, 1), (1027, 9, 3), (4096, 33, 1)])
+                                     (1024, 1, 1), (1027, 9, 3), (4096, 33, 1),
+                                     # rows of whole 16-byte vectors: the one-pass kernel
+                                     (16, 5, 3), (32, 7, 4), (48, 3, 1), (80, 9, 3), (4000, 6, 4),
+                                     (2736, 11, 3)])
 def test_random_geometries(S, O, W, H, Cch):
     rng = np.random.default_rng(W * 131 + H * 7 + Cch)
     cover = rng.integers(0, 256, W * H * Cch, dtype=np.uint8)
@@ -105,3 +108,31 @@ def test_geometry_errors(S):
     with pytest.raises(S.StegoError) as e:
         S.stego_embed(c, s, m, S.LAYOUT_PAPER2 | S.HEADER_BE32, geom=(8, 4, 3, 0))
     assert e.value.status == S.E_INVAL
+
+
+def test_full_size_8192_plane0(S, O):
+    """8192x8192x3 cover, plane 0, message at the full floor(W/4)*H capacity
+    (16,777,216 bytes): one-pass out of place, in place, extraction, all
+    against the oracle over every byte."""
+    from paper_0912_0947_gb300 import synth
+    W = H = 8192
+    C = W * H * 3
+    N = (W // 4) * H
+    cover = synth.uniform_bytes(C, 0xC0FFEE21, "cuda")
+    msg = synth.uniform_bytes(N, 0xC0FFEE22, "cuda")
+    geom = (W, H, 3, 0)
+    stego = torch.empty_like(cover)
+    res = S.new_result()
+    S.stego_embed(cover, stego, msg, S.LAYOUT_PAPER2 | S.FUSE_STATS, res, geom=geom)
+    c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+    st, want = O.paper2_embed(c_h, W, H, 3, 0, m_h)
+    assert st == 0
+    assert np.array_equal(stego.cpu().numpy(), want)
+    r = S.read_result(res)
+    assert (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+    buf = cover.clone()
+    S.stego_embed(buf, buf, msg, S.LAYOUT_PAPER2, geom=geom)
+    assert torch.equal(buf, stego)
+    out = torch.empty(N, dtype=torch.uint8, device="cuda")
+    S.stego_extract(stego, out, N, S.LAYOUT_PAPER2, geom=geom)
+    assert torch.equal(out, msg)
