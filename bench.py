@@ -108,6 +108,28 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
+# multi-rank aggregation (replicas: every rank runs its own cover)
+# ----------------------------------------------------------------------------
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest per-rank value (the slowest rank bounds the job); a
+    timing reduction only, no data moves between ranks."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank: float, max_ms: float, world: int) -> float:
+    """Whole-job GB/s: the bytes every rank processed over the slowest rank's
+    time."""
+    return world * bytes_per_rank / (max_ms / 1e3) / 1e9
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 
@@ -189,12 +211,8 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     t_emb = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]  # ms
     t_ext = [evs[k][2].elapsed_time(evs[k][3]) for k in range(args.steps)]
-    dev_ms = sum(t_emb) + sum(t_ext)
-    if world > 1:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    value = world * 2.0 * C * args.steps / (dev_ms / 1e3) / 1e9
+    dev_ms = max_over_ranks(sum(t_emb) + sum(t_ext), world, dev)
+    value = job_throughput(2.0 * C * args.steps, dev_ms, world)
 
     stats = S.read_result(res_e)
     # ---- end to end through the public API with host buffers ---------------

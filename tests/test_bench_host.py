@@ -1,0 +1,101 @@
+"""Host-side logic of bench.py and the autotuner, on CPU: the multi-rank
+timing reduction (two gloo ranks), the reference arm's rank handling and its
+JSON line, and the autotuner's choice, restore and cache."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu")
+    q.put((rank, ms, bench.job_throughput(1e9, ms, world)))
+    dist.destroy_process_group()
+
+
+def test_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [15.0, 15.0]  # both ranks see the slowest
+    assert out[0][2] == pytest.approx(2 * 1e9 / 0.015 / 1e9)
+
+
+def test_single_rank_is_identity():
+    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
+    assert bench.job_throughput(2e9, 1000.0, 1) == pytest.approx(2.0)
+
+
+def test_reference_arm_only_on_rank0():
+    class A:
+        steps, warmup, ref_seconds = 3, 3, 1.0
+    assert bench.run_reference(A, 1, 2) is None
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "3",
+                        "--warmup", "3", "--ref-seconds", "1"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "cover GB/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+    assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
+
+
+def test_autotune_picks_restores_and_caches(tmp_path, monkeypatch):
+    import paper_0912_0947_gb300 as S
+    from paper_0912_0947_gb300 import autotune as AT
+    from paper_0912_0947_gb300 import build as B
+    try:
+        B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    B.build()
+    monkeypatch.setenv("STEGO_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=None: "FakeGPU")
+    seen = []
+
+    def fake_time(fn, flush, reps=15, stream=None):
+        t = S.stego_get_tune(S.OP_EXTRACT)
+        seen.append((t.threads, t.vec_per_thread, t.ctas_per_sm))
+        # fastest at 256 threads, 8 vectors, 2 CTAs per SM
+        return abs(t.threads - 256) / 64 + abs(t.vec_per_thread - 8) + abs(t.ctas_per_sm - 2) + 10.0
+
+    monkeypatch.setattr(AT, "time_call", fake_time)
+    old = S.stego_get_tune(S.OP_EXTRACT)
+    try:
+        best, us, table = AT.autotune(S.OP_EXTRACT, lambda: None, 1 << 27, flush=lambda: None,
+                                      use_cache=False)
+        assert best[:3] == (256, 8, 2) and us == 10.0 and len(table) == len(AT.SINGLE_CANDIDATES)
+        t = S.stego_get_tune(S.OP_EXTRACT)
+        assert (t.threads, t.vec_per_thread, t.ctas_per_sm) == (256, 8, 2)  # installed
+        assert len(set(seen)) == len(AT.SINGLE_CANDIDATES)
+        S.stego_set_tune(S.OP_EXTRACT, (128, 2, 0, 0))
+        hit = AT.load_cached(S.OP_EXTRACT, 1 << 27)  # same size class: cached and installed
+        assert hit["shape"][:3] == [256, 8, 2]
+        t = S.stego_get_tune(S.OP_EXTRACT)
+        assert (t.threads, t.vec_per_thread, t.ctas_per_sm) == (256, 8, 2)
+        assert AT.load_cached(S.OP_EXTRACT, 1 << 20) is None  # other size class
+    finally:
+        S.stego_set_tune(S.OP_EXTRACT, old)

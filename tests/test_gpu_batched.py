@@ -224,3 +224,53 @@ def test_video_frames(S, O):
     descs = S.descs_to_device(S.pack_descs(recs))
     S.stego_extract_batched(descs, F, res, 0, ws)
     assert torch.equal(out, stream), "concatenated per-frame extracts give the stream back"
+
+
+def test_uneven_4096_full_size(S, O):
+    """4096 covers, sides log-uniform in [64, 4096], 1 or 3 channels,
+    messages at 5..100 % of capacity (about 8 GB), in one persistent launch:
+    sampled covers against the oracle byte for byte; on every cover only LSBs
+    change and the batched extraction returns the message."""
+    items = synth.uneven_batch(4096)
+    sizes = [it.cover_bytes for it in items]
+    mlens = [it.msg_bytes for it in items]
+    off, moff, p, q = [], [], 0, 0
+    for c, m in zip(sizes, mlens):
+        off.append(p)
+        moff.append(q)
+        p += (c + 255) // 256 * 256
+        q += (m + 255) // 256 * 256
+    covers = synth.uniform_bytes(p, synth.substream(synth.SEED_BASE + 4, 1), "cuda")
+    msgs = synth.uniform_bytes(q, synth.substream(synth.SEED_BASE + 4, 2), "cuda")
+    stego = covers.clone()  # padding between slots is never written: keep it equal
+    n = len(sizes)
+    cv = [covers[o:o + c] for o, c in zip(off, sizes)]
+    sv = [stego[o:o + c] for o, c in zip(off, sizes)]
+    mv = [msgs[o:o + m] for o, m in zip(moff, mlens)]
+    descs = S.descs_to_device(S.pack_descs(
+        [dict(cover=cv[i], stego=sv[i], msg=mv[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]))
+    res = S.new_result(n=n)
+    ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(descs, n, res, S.FUSE_STATS, ws)
+    rr = S.read_result(res)
+    assert all(r["status"] == 0 and r["msg_bytes"] == mlens[i] for i, r in enumerate(rr))
+    for i in list(range(0, n, 409)) + [int(np.argmax(sizes)), int(np.argmin(sizes))]:
+        c = cv[i].cpu().numpy()
+        st, want = O.stream1_embed(c, mv[i].cpu().numpy(), header=True)
+        assert st == 0 and np.array_equal(sv[i].cpu().numpy(), want), i
+        assert (rr[i]["changed"], rr[i]["sse"]) == O.changed_bytes(c, want)
+    assert not bool(((stego ^ covers) & 0xFE).any())
+    out = torch.zeros_like(msgs)
+    ov = [out[o:o + m] for o, m in zip(moff, mlens)]
+    descs_x = S.descs_to_device(S.pack_descs(
+        [dict(cover=sv[i], msg=ov[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]))
+    S.stego_extract_batched(descs_x, n, res, 0, ws)
+    rr = S.read_result(res)
+    assert all(r["status"] == 0 and r["msg_bytes"] == mlens[i] for i, r in enumerate(rr))
+    assert all(torch.equal(ov[i], mv[i]) for i in range(n))
+    # bytes past each message's carrying region are the cover's
+    for i in range(0, n, 97):
+        T = 8 * (mlens[i] + 4)
+        assert torch.equal(sv[i][T:], cv[i][T:])
