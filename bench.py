@@ -223,14 +223,15 @@ def run_ours(args, rank, world, local_rank):
     # ---- batched vs one launch per image -----------------------------------------
     legs = {}
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
-                                                         "paper2", "serving"}
+                                                         "batched_video_paper2", "paper2",
+                                                         "serving"}
     if args.no_batched:
-        want -= {"batched_uneven", "batched_video", "paper2"}
+        want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2"}
     if args.no_serving:
         want.discard("serving")
     del flush
     torch.cuda.empty_cache()
-    for kind in ("uneven", "video"):
+    for kind in ("uneven", "video", "video_paper2"):
         if rank == 0 and "batched_" + kind in want:
             legs["batched_" + kind] = run_batched_leg(
                 S, AT, torch, dev, stream, synth, kind,
@@ -311,6 +312,7 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
             messages filling 5..100 % of capacity;
     video:  600 frames of 1920x1080x3, gradient plus noise, one message
             stream split across frames at half capacity, header per frame."""
+    paper = kind == "video_paper2"
     if kind == "uneven":
         items = synth.uneven_batch(count or 4096)
         sizes = [it.cover_bytes for it in items]
@@ -352,13 +354,15 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
     mv = [msgs[o:o + m] for o, m in zip(moff, mlens)]
     ob = [out_b[o:o + m] for o, m in zip(moff, mlens)]
     o1 = [out_1[o:o + m] for o, m in zip(moff, mlens)]
-    hdr = S.HEADER_BE32
+    hdr = S.LAYOUT_PAPER2 if paper else S.HEADER_BE32
+    geo = dict(width=v.width, height=v.height, channels=3, plane=0) if paper else {}
+    geom = (v.width, v.height, 3, 0) if paper else None
     d_emb = S.descs_to_device(S.pack_descs(
         [dict(cover=cv[i], stego=sb[i], msg=mv[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
-              flags=hdr) for i in range(n)]), dev)
+              flags=hdr, **geo) for i in range(n)]), dev)
     d_ext = S.descs_to_device(S.pack_descs(
-        [dict(cover=sb[i], msg=ob[i], cover_bytes=sizes[i], msg_bytes=mlens[i], flags=hdr)
-         for i in range(n)]), dev)
+        [dict(cover=sb[i], msg=ob[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              msg_len=mlens[i], flags=hdr, **geo) for i in range(n)]), dev)
     res_b = S.new_result(dev, n=n)
     res_1 = S.new_result(dev, n=n)
     res_x1 = S.new_result(dev, n=n)
@@ -373,11 +377,12 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
 
     def one_embed():
         for i in range(n):
-            S.stego_embed(cv[i], s1[i], mv[i], hdr | S.FUSE_STATS, res_1[i], stream=stream)
+            S.stego_embed(cv[i], s1[i], mv[i], hdr | S.FUSE_STATS, res_1[i], geom=geom,
+                          stream=stream)
 
     def one_extract():
         for i in range(n):
-            S.stego_extract(s1[i], o1[i], 0, hdr, res_x1[i], stream=stream)
+            S.stego_extract(s1[i], o1[i], mlens[i], hdr, res_x1[i], geom=geom, stream=stream)
 
     tune_sel = {}
     for name, op, fn in (("embed", S.OP_EMBED_BATCHED, b_embed),
@@ -400,15 +405,22 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
     assert same, "batched and per-image outputs differ"
     assert all(torch.equal(ob[i], mv[i]) for i in range(n)), "batched round trip differs"
     total = sum(sizes)
-    T = [8 * (m + 4) for m in mlens]
-    emb_bytes = sum(2 * c + t // 8 for c, t in zip(sizes, T))
-    ext_bytes = sum(t + t // 8 for t in T)
+    if paper:  # out of place 2C + N; extraction touches every sector of its rows
+        emb_bytes = sum(2 * c + m for c, m in zip(sizes, mlens))
+        rows = [-(-m // (v.width // 4)) for m in mlens]
+        ext_bytes = sum(r * v.width * 3 + m for r, m in zip(rows, mlens))
+    else:
+        T = [8 * (m + 4) for m in mlens]
+        emb_bytes = sum(2 * c + t // 8 for c, t in zip(sizes, T))
+        ext_bytes = sum(t + t // 8 for t in T)
     peak, _ = hbm_peak()
     gbs = lambda b, us: round(b / (us * 1e-6) / 1e9, 1)
     return {
         "workload": ("4096 uneven covers (log-uniform sides 64..4096, 1 or 3 channels, "
                      "5-100% fill)" if kind == "uneven" else
-                     "600 frames 1920x1080x3, gradient+noise, half capacity per frame"),
+                     ("%d frames 1920x1080x3, gradient+noise, paper layout (plane 0, 2 bits/byte), "
+                      "388796 message bytes per frame" % n) if paper else
+                     "%d frames 1920x1080x3, gradient+noise, half capacity per frame" % n),
         "covers": n, "cover_bytes": total,
         "embed_batched_us": round(t_be, 1), "embed_graph_us": round(t_ge, 1),
         "embed_per_image_us": round(t_1e, 1),

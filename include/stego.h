@@ -230,6 +230,9 @@ uint64_t stego_batched_workspace_bytes(uint32_t n);
  *              stego_batched_workspace_bytes(n), 16-byte aligned.  It is
  *              scratch: its contents on entry do not matter and on return
  *              are unspecified.
+ * Both layouts may be mixed in one batch.  One-bit stream covers are cut
+ * into tiles of cover bytes; paper-layout covers into tiles of whole rows
+ * (out of place: rows are copied, then their plane bytes rewritten).
  * Descriptor errors (capacity, geometry, overlap) are per cover: that
  * cover's status is set and its output is not written; other covers
  * proceed.  Returns STEGO_E_NOMEM when ws_bytes is too small. */
@@ -251,7 +254,7 @@ int stego_extract_batched(const stego_desc *d_descs, uint32_t n, stego_result *d
  *   n  at most STEGO_NOALLOC_MAX_DESCS; larger batches return
  *      STEGO_E_NOMEM and nothing is launched.
  * Other arguments, results and per-cover errors as for stego_embed_batched.
- * The scratch array (about 320 KiB) is one per GPU, held by every GPU that
+ * The scratch array (about 640 KiB) is one per GPU, held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * sets up that device (it looks up the array's device address with
  * cudaGetSymbolAddress); make that first call before any stream capture.

@@ -19,37 +19,62 @@
 // Workspace (caller-owned scratch, 16-byte aligned):
 //   [0, 64)                 head: total tiles, work counter
 //   [64, 64 + 8(n+1))       tile offsets (counts before the scan)
-//   [info_off, +32n)        per-descriptor derived sizes and flags
+//   [info_off, +64n)        per-descriptor derived sizes, geometry and mode
+// Both layouts batch: the one-bit stream in tiles of cover bytes; the
+// paper's layout (Sections VI/VII) in tiles of whole rows (copy, barrier,
+// scatter out of place; scatter in place) and, for extraction, of 16-byte
+// message runs (1, 3 or 4 channels) or rows, with the routines the
+// single-image kernels use.  The paper layout has its own persistent
+// kernels (own tile offsets and counter), so its register needs do not
+// touch the stream kernels'.
 #include <cstring>
 #include <mutex>
 
+#include "p2_device.cuh"
 #include "s1_device.cuh"
 
 namespace stego {
 namespace {
 
 struct WsHead {
-    unsigned long long total;
+    unsigned long long total;     // one-bit stream tiles
     unsigned long long counter;
-    unsigned long long pad[6];
+    unsigned long long total_p;   // paper-layout tiles
+    unsigned long long counter_p;
+    unsigned long long pad[4];
 };
 
 struct DescInfo {
-    uint64_t n_bytes; // embed: bytes written; extract: carrying bytes 8*len
-    uint64_t t_bytes; // embed: carrying bytes
-    uint64_t len;     // embed: stream bytes; extract: message bytes
+    uint64_t n_bytes; // stream embed: bytes written; stream extract: 8*len
+    uint64_t t_bytes; // stream embed: carrying bytes
+    uint64_t len;     // stream embed: stream bytes; extract / paper: message bytes
     uint32_t nbits;   // header value
     uint32_t bits;    // kHeader | kVec | kMsgEven
+    uint32_t W, H;    // paper layout geometry
+    uint32_t channels, plane;
+    uint32_t mode;     // paper layout: one of the kP2* work kinds
+    uint32_t per_tile; // paper layout: units, rows or runs per tile
+    uint32_t pad[2];
 };
+static_assert(sizeof(DescInfo) == 64, "DescInfo is 64 bytes");
 
 constexpr uint32_t kHeader = 1u, kVec = 2u, kMsgEven = 4u;
+// paper-layout work kinds (0 = the one-bit stream layout)
+constexpr uint32_t kP2Units = 1u, kP2RowsCopy = 2u, kP2Rows = 3u, kP2Runs = 4u, kP2RowsX = 5u;
 constexpr uint32_t kChunk = 4u; // tiles per claim
 
-uint64_t info_off(uint32_t n) { return (64ull + 8ull * ((uint64_t)n + 1) + 15ull) & ~15ull; }
+// Workspace: head (64 B), stream tile offsets (n+1), paper tile offsets
+// (n+1), per-descriptor info (64 B each, 16-byte aligned).
+constexpr uint64_t startp_off(uint32_t n) { return 64ull + 8ull * ((uint64_t)n + 1); }
+constexpr uint64_t info_off(uint32_t n)
+{
+    return (64ull + 16ull * ((uint64_t)n + 1) + 15ull) & ~15ull;
+}
 
 struct WsView {
     WsHead *head;
-    unsigned long long *start;
+    unsigned long long *start;   // stream-layout tile offsets
+    unsigned long long *start_p; // paper-layout tile offsets
     DescInfo *info;
 };
 
@@ -58,6 +83,7 @@ WsView ws_view(void *ws, uint32_t n)
     WsView v;
     v.head = reinterpret_cast<WsHead *>(ws);
     v.start = reinterpret_cast<unsigned long long *>((char *)ws + 64);
+    v.start_p = reinterpret_cast<unsigned long long *>((char *)ws + startp_off(n));
     v.info = reinterpret_cast<DescInfo *>((char *)ws + info_off(n));
     return v;
 }
@@ -76,6 +102,41 @@ __device__ __forceinline__ bool d_aligned16(const void *p) { return ((uintptr_t)
 // 1. prep
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ void clear_info(DescInfo &inf)
+{
+    inf.n_bytes = inf.t_bytes = inf.len = 0;
+    inf.nbits = inf.bits = 0;
+    inf.W = inf.H = inf.channels = inf.plane = 0;
+    inf.mode = inf.per_tile = 0;
+    inf.pad[0] = inf.pad[1] = 0;
+}
+
+// Paper-layout geometry of a descriptor: channels > 0, plane < channels and
+// width * height * channels == cover_bytes (Section VI step 2).
+__device__ __forceinline__ bool paper_geom_ok(const stego_desc &D)
+{
+    const stego_geom &g = D.geom;
+    return g.channels > 0 && g.plane < g.channels &&
+           (uint64_t)g.width * g.height * g.channels == D.cover_bytes;
+}
+
+__device__ __forceinline__ void paper_info(const stego_desc &D, DescInfo &inf, uint64_t N)
+{
+    inf.len = N;
+    inf.W = D.geom.width;
+    inf.H = D.geom.height;
+    inf.channels = D.geom.channels;
+    inf.plane = D.geom.plane;
+}
+
+// Whole rows per tile for the row-based work kinds (at least one).
+__device__ __forceinline__ uint64_t rows_for(const stego_desc &D, uint32_t tile_bytes)
+{
+    const uint64_t rb = (uint64_t)D.geom.width * D.geom.channels;
+    const uint64_t r = rb ? tile_bytes / rb : 1u;
+    return r ? r : 1u;
+}
+
 __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *results, WsView ws,
                            uint32_t tile_bytes)
 {
@@ -87,8 +148,8 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
         int st = STEGO_OK;
         if (D.flags & ~(STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS))
             st = STEGO_E_INVAL;
-        else if (layout != STEGO_LAYOUT_STREAM1)
-            st = STEGO_E_INVAL; // the batched path carries the one-bit stream layout
+        else if (layout != STEGO_LAYOUT_STREAM1 && layout != STEGO_LAYOUT_PAPER2)
+            st = STEGO_E_INVAL;
         else if (D.cover_bytes > 0 && (!D.cover || !D.stego))
             st = STEGO_E_INVAL;
         else if (D.msg_bytes > 0 && !D.msg)
@@ -97,7 +158,12 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
             st = STEGO_E_INVAL;
         else if (d_overlap(D.msg, D.msg_bytes, D.stego, D.cover_bytes))
             st = STEGO_E_INVAL;
-        else {
+        else if (layout == STEGO_LAYOUT_PAPER2) {
+            if (header || !paper_geom_ok(D))
+                st = STEGO_E_INVAL;
+            else if (D.msg_bytes > (uint64_t)(D.geom.width / 4u) * D.geom.height)
+                st = STEGO_E_CAPACITY;
+        } else {
             uint64_t cap = D.cover_bytes / 8u;
             if (header) {
                 cap = cap >= 4u ? cap - 4u : 0u;
@@ -108,11 +174,33 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
                 st = STEGO_E_CAPACITY;
         }
         DescInfo inf;
-        inf.n_bytes = inf.t_bytes = inf.len = 0;
-        inf.nbits = 0;
-        inf.bits = 0;
+        clear_info(inf);
         unsigned long long tiles = 0;
-        if (st == STEGO_OK) {
+        if (st == STEGO_OK && layout == STEGO_LAYOUT_PAPER2) {
+            paper_info(D, inf, D.msg_bytes);
+            const uint32_t ch = D.geom.channels;
+            const uint64_t rows_per_tile = rows_for(D, tile_bytes);
+            const p2::View v = p2::make_view(nullptr, nullptr, D.geom.width, D.geom.height, ch,
+                                             D.geom.plane, nullptr, nullptr, D.msg_bytes);
+            if (!inplace && d_aligned16(D.cover) && d_aligned16(D.stego) &&
+                (ch == 3 || ch == 1) && D.geom.plane == 0 && D.geom.width % 16u == 0 &&
+                (uint64_t)D.geom.width / 16u * D.geom.height < (1ull << 31)) {
+                // one-pass units for the common planes: RGB plane 0, grayscale
+                const uint64_t units = (uint64_t)(D.geom.width / 16u) * D.geom.height;
+                const uint64_t per = tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u;
+                inf.mode = kP2Units;
+                inf.per_tile = (uint32_t)per;
+                tiles = (units + per - 1) / per;
+            } else if (!inplace) {
+                inf.mode = kP2RowsCopy;
+                inf.per_tile = (uint32_t)rows_per_tile;
+                tiles = (D.geom.height + rows_per_tile - 1) / rows_per_tile;
+            } else {
+                inf.mode = kP2Rows;
+                inf.per_tile = (uint32_t)rows_per_tile;
+                tiles = (v.R + rows_per_tile - 1) / rows_per_tile;
+            }
+        } else if (st == STEGO_OK) {
             inf.len = D.msg_bytes + (header ? 4u : 0u);
             inf.t_bytes = 8u * inf.len;
             inf.n_bytes = inplace ? inf.t_bytes : D.cover_bytes;
@@ -123,7 +211,8 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
             tiles = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
         }
         ws.info[d] = inf;
-        ws.start[d] = tiles;
+        ws.start[d] = inf.mode ? 0ull : tiles;
+        ws.start_p[d] = inf.mode ? tiles : 0ull;
         stego_result r;
         r.changed = 0;
         r.sse = 0;
@@ -146,7 +235,9 @@ __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *
         uint32_t nbits = 0;
         if (D.flags & ~(STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS))
             st = STEGO_E_INVAL;
-        else if (layout != STEGO_LAYOUT_STREAM1)
+        else if (layout != STEGO_LAYOUT_STREAM1 && layout != STEGO_LAYOUT_PAPER2)
+            st = STEGO_E_INVAL;
+        else if (layout == STEGO_LAYOUT_PAPER2 && (header || !paper_geom_ok(D)))
             st = STEGO_E_INVAL;
         else if (D.cover_bytes > 0 && !D.cover)
             st = STEGO_E_INVAL;
@@ -154,7 +245,13 @@ __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *
             st = STEGO_E_INVAL;
         else if (d_overlap(D.msg, D.msg_bytes, D.cover, D.cover_bytes))
             st = STEGO_E_INVAL;
-        else if (header) {
+        else if (layout == STEGO_LAYOUT_PAPER2) {
+            len = D.msg_len;
+            if (len > (uint64_t)(D.geom.width / 4u) * D.geom.height)
+                st = STEGO_E_CAPACITY;
+            else if (len > D.msg_bytes)
+                st = STEGO_E_MSG_TOO_SMALL;
+        } else if (header) {
             if (D.cover_bytes < 32) {
                 st = STEGO_E_BAD_HEADER;
             } else {
@@ -173,14 +270,37 @@ __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *
         if (st != STEGO_OK)
             len = 0;
         DescInfo inf;
-        inf.len = len;
-        inf.n_bytes = 8u * len;
-        inf.t_bytes = 0;
-        inf.nbits = nbits;
-        inf.bits = (header ? kHeader : 0u) | (d_aligned16(D.cover) ? kVec : 0u) |
-                   ((((uintptr_t)D.msg & 1u) == 0) ? kMsgEven : 0u);
+        clear_info(inf);
+        unsigned long long tiles = 0;
+        if (layout == STEGO_LAYOUT_PAPER2 && st == STEGO_OK) {
+            paper_info(D, inf, len);
+            const p2::View v = p2::make_view(nullptr, nullptr, D.geom.width, D.geom.height,
+                                             D.geom.channels, D.geom.plane, nullptr, nullptr, len);
+            if (p2::unit_channels(D.geom.channels)) {
+                const uint64_t runs = (uint64_t)((v.Q + 15) / 16) * v.R;
+                const uint64_t per = tile_bytes / (64u * D.geom.channels)
+                                         ? tile_bytes / (64u * D.geom.channels)
+                                         : 1u;
+                inf.mode = kP2Runs;
+                inf.per_tile = (uint32_t)per;
+                tiles = (runs + per - 1) / per;
+            } else {
+                const uint64_t per = rows_for(D, tile_bytes);
+                inf.mode = kP2RowsX;
+                inf.per_tile = (uint32_t)per;
+                tiles = (v.R + per - 1) / per;
+            }
+        } else {
+            inf.len = len;
+            inf.n_bytes = 8u * len;
+            inf.nbits = nbits;
+            inf.bits = (header ? kHeader : 0u) | (d_aligned16(D.cover) ? kVec : 0u) |
+                       ((((uintptr_t)D.msg & 1u) == 0) ? kMsgEven : 0u);
+            tiles = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
+        }
         ws.info[d] = inf;
-        ws.start[d] = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
+        ws.start[d] = inf.mode ? 0ull : tiles;
+        ws.start_p[d] = inf.mode ? tiles : 0ull;
         stego_result r;
         r.changed = 0;
         r.sse = 0;
@@ -197,16 +317,18 @@ __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *
 
 constexpr int kScanThreads = 1024;
 
-__global__ void __launch_bounds__(kScanThreads) scan_tiles(WsView ws, uint32_t n)
+// Exclusive scan of counts[0..n) in place, counts[n] = total; the calling
+// CTA's kScanThreads threads together.
+__device__ __forceinline__ unsigned long long scan_one(unsigned long long *counts, uint32_t n,
+                                                      unsigned long long *part)
 {
-    __shared__ unsigned long long part[kScanThreads];
     const uint32_t t = threadIdx.x, T = blockDim.x;
     const uint64_t seg = ((uint64_t)n + T - 1) / T;
     const uint64_t b = (uint64_t)t * seg;
     const uint64_t e = b + seg < n ? b + seg : n;
     unsigned long long sum = 0;
     for (uint64_t i = b; i < e; ++i)
-        sum += ws.start[i];
+        sum += counts[i];
     part[t] = sum;
     __syncthreads();
     for (uint32_t off = 1; off < T; off <<= 1) {
@@ -217,14 +339,27 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles(WsView ws, uint32_t n
     }
     unsigned long long run = part[t] - sum;
     for (uint64_t i = b; i < e; ++i) {
-        const unsigned long long c = ws.start[i];
-        ws.start[i] = run;
+        const unsigned long long c = counts[i];
+        counts[i] = run;
         run += c;
     }
-    if (t == T - 1) {
-        ws.start[n] = part[T - 1];
-        ws.head->total = part[T - 1];
+    const unsigned long long total = part[T - 1];
+    if (t == T - 1)
+        counts[n] = total;
+    __syncthreads(); // part[] is reused by the next scan
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles(WsView ws, uint32_t n)
+{
+    __shared__ unsigned long long part[kScanThreads];
+    const unsigned long long ts = scan_one(ws.start, n, part);
+    const unsigned long long tp = scan_one(ws.start_p, n, part);
+    if (threadIdx.x == 0) {
+        ws.head->total = ts;
         ws.head->counter = 0;
+        ws.head->total_p = tp;
+        ws.head->counter_p = 0;
     }
 }
 
@@ -269,12 +404,13 @@ __device__ __forceinline__ void flush_stats(unsigned long long &changed, unsigne
 // The claim loop shared by both directions: calls body(d, local_tile) for
 // every tile this CTA claims, in order.
 template <typename Body>
-__device__ __forceinline__ void claim_loop(const WsView &ws, uint32_t n, Body &&body)
+__device__ __forceinline__ void claim_loop(const unsigned long long *start,
+                                           unsigned long long total,
+                                           unsigned long long *counter, uint32_t n, Body &&body)
 {
     __shared__ unsigned long long s_claim;
-    const unsigned long long total = ws.head->total;
     if (threadIdx.x == 0)
-        s_claim = atomicAdd(&ws.head->counter, (unsigned long long)kChunk);
+        s_claim = atomicAdd(counter, (unsigned long long)kChunk);
     __syncthreads();
     for (;;) {
         const unsigned long long c0 = s_claim;
@@ -282,15 +418,58 @@ __device__ __forceinline__ void claim_loop(const WsView &ws, uint32_t n, Body &&
         if (c0 >= total)
             break;
         if (threadIdx.x == 0) // next claim in flight while this chunk runs
-            s_claim = atomicAdd(&ws.head->counter, (unsigned long long)kChunk);
+            s_claim = atomicAdd(counter, (unsigned long long)kChunk);
         const unsigned long long c1 = c0 + kChunk < total ? c0 + kChunk : total;
-        uint32_t d = owner_of(ws.start, n, c0);
+        uint32_t d = owner_of(start, n, c0);
         for (unsigned long long t = c0; t < c1; ++t) {
-            while (ws.start[d + 1] <= t)
+            while (start[d + 1] <= t)
                 ++d;
-            body(d, t - ws.start[d]);
+            body(d, t - start[d]);
         }
         __syncthreads(); // the next claim is visible
+    }
+}
+
+// One tile of a paper-layout cover (the CTA's threads together).
+template <bool STATS>
+__device__ __forceinline__ void paper_embed_tile(const stego_desc &D, const DescInfo &inf,
+                                                 unsigned long long lt,
+                                                 unsigned long long &changed,
+                                                 unsigned long long &sse)
+{
+    const p2::View v = p2::make_view(D.cover, D.stego, inf.W, inf.H, inf.channels, inf.plane,
+                                     D.msg, nullptr, inf.len);
+    const uint64_t b0 = lt * inf.per_tile, b1 = b0 + inf.per_tile;
+    if (inf.mode == kP2Units) {
+        const uint64_t units = (uint64_t)(inf.W / 16u) * inf.H;
+        const uint32_t k0 = (uint32_t)b0 + threadIdx.x;
+        const uint32_t k1 = (uint32_t)(b1 < units ? b1 : units);
+        if (inf.channels == 3)
+            p2::units_embed<3, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
+        else
+            p2::units_embed<1, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
+        return;
+    }
+    const uint32_t r0 = (uint32_t)b0;
+    const uint32_t r1 = (uint32_t)(b1 < inf.H ? b1 : inf.H);
+    if (inf.mode == kP2RowsCopy) {
+        p2::rows_copy(v, r0, r1);
+        __syncthreads(); // the copy lands before the scatter overwrites plane bytes
+    }
+    p2::rows_embed<STATS>(v, r0, r1, 1, changed, sse);
+}
+
+__device__ __forceinline__ void paper_extract_tile(const stego_desc &D, const DescInfo &inf,
+                                                   unsigned long long lt)
+{
+    const p2::View v = p2::make_view(D.cover, nullptr, inf.W, inf.H, inf.channels, inf.plane,
+                                     nullptr, D.msg, inf.len);
+    const uint64_t b0 = lt * inf.per_tile, b1 = b0 + inf.per_tile;
+    if (inf.mode == kP2Runs) {
+        const uint64_t runs = (uint64_t)((v.Q + 15) / 16) * v.R;
+        p2::runs_extract_any(v, b0 + threadIdx.x, b1 < runs ? b1 : runs, blockDim.x);
+    } else {
+        p2::rows_extract(v, (uint32_t)b0, (uint32_t)(b1 < v.R ? b1 : v.R), 1);
     }
 }
 
@@ -301,7 +480,8 @@ __global__ void __launch_bounds__(512) persist_embed(const stego_desc *descs, ui
 {
     unsigned long long changed = 0, sse = 0;
     uint32_t stat_d = 0xFFFFFFFFu;
-    claim_loop(ws, n, [&](uint32_t d, unsigned long long lt) {
+    claim_loop(ws.start, ws.head->total, &ws.head->counter, n,
+               [&](uint32_t d, unsigned long long lt) {
         if (STATS && d != stat_d) {
             flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
             stat_d = d;
@@ -339,7 +519,8 @@ template <int V>
 __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, uint32_t n,
                                                        WsView ws, uint32_t tile_bytes)
 {
-    claim_loop(ws, n, [&](uint32_t d, unsigned long long lt) {
+    claim_loop(ws.start, ws.head->total, &ws.head->counter, n,
+               [&](uint32_t d, unsigned long long lt) {
         const stego_desc &D = descs[d];
         const DescInfo inf = ws.info[d];
         s1::ExtractView x;
@@ -358,6 +539,35 @@ __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, 
         } else {
             s1::extract_bytes_range(x, (b0 >> 3) + threadIdx.x, b1 >> 3, blockDim.x);
         }
+    });
+}
+
+// The paper layout's own persistent kernels (a separate register budget from
+// the stream kernels): tiles of units, rows or runs, claimed like above.
+template <bool STATS>
+__global__ void __launch_bounds__(256) persist_p2_embed(const stego_desc *descs, uint32_t n,
+                                                        stego_result *results, WsView ws)
+{
+    unsigned long long changed = 0, sse = 0;
+    uint32_t stat_d = 0xFFFFFFFFu;
+    claim_loop(ws.start_p, ws.head->total_p, &ws.head->counter_p, n,
+               [&](uint32_t d, unsigned long long lt) {
+        if (STATS && d != stat_d) {
+            flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+            stat_d = d;
+        }
+        paper_embed_tile<STATS>(descs[d], ws.info[d], lt, changed, sse);
+    });
+    if (STATS)
+        flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+}
+
+__global__ void __launch_bounds__(256) persist_p2_extract(const stego_desc *descs, uint32_t n,
+                                                          WsView ws)
+{
+    claim_loop(ws.start_p, ws.head->total_p, &ws.head->counter_p, n,
+               [&](uint32_t d, unsigned long long lt) {
+        paper_extract_tile(descs[d], ws.info[d], lt);
     });
 }
 
@@ -431,6 +641,21 @@ int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint
     } else {
         void *args[] = {(void *)&d_descs, &n, &ws, (void *)&tile};
         e = cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+    }
+    if (e != cudaSuccess)
+        return STEGO_E_CUDA;
+    // paper-layout tiles (their count is on the device; an empty set exits at once)
+    const int p2_threads = 256;
+    const void *kp = EMBED ? (stats ? (const void *)persist_p2_embed<true>
+                                    : (const void *)persist_p2_embed<false>)
+                           : (const void *)persist_p2_extract;
+    const int gridp = persistent_grid(kp, p2_threads, 0, 0, ~0ull >> 1, 1);
+    if (EMBED) {
+        void *args[] = {(void *)&d_descs, &n, &d_results, &ws};
+        e = cudaLaunchKernel(kp, dim3(gridp), dim3(p2_threads), args, 0, s);
+    } else {
+        void *args[] = {(void *)&d_descs, &n, &ws};
+        e = cudaLaunchKernel(kp, dim3(gridp), dim3(p2_threads), args, 0, s);
     }
     return e == cudaSuccess ? STEGO_OK : STEGO_E_CUDA;
 }
@@ -538,7 +763,7 @@ namespace {
 
 constexpr uint32_t kNoAllocMaxDescs = STEGO_NOALLOC_MAX_DESCS;
 constexpr uint64_t kNoAllocBytes =
-    ((64ull + 8ull * (kNoAllocMaxDescs + 1ull) + 15ull) & ~15ull) + 32ull * kNoAllocMaxDescs;
+    stego::info_off(kNoAllocMaxDescs) + sizeof(stego::DescInfo) * (uint64_t)kNoAllocMaxDescs;
 constexpr int kNoAllocDevices = 64;
 
 std::mutex g_noalloc_mu;

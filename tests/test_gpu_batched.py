@@ -274,3 +274,127 @@ def test_uneven_4096_full_size(S, O):
     for i in range(0, n, 97):
         T = 8 * (mlens[i] + 4)
         assert torch.equal(sv[i][T:], cv[i][T:])
+
+
+def test_batched_paper_layout_mixed_with_stream(S, O):
+    """Paper-layout covers (Sections VI/VII) in the same batches as one-bit
+    stream covers: out of place and in place, aligned and misaligned
+    buffers, several geometries and planes, per-cover errors; batched
+    extraction with the out-of-band length."""
+    rng = np.random.default_rng(41)
+    geoms = [(16, 5, 3, 1), (1920, 9, 3, 0), (33, 7, 3, 2), (64, 16, 4, 3), (1024, 3, 1, 0),
+             (9, 4, 3, 1), (4000, 6, 4, 2), (7, 3, 2, 1), (3, 4, 1, 0)]
+    recs, want, covers, kinds = [], [], [], []
+    keep = []
+    for gi, (W, H, C, pl) in enumerate(geoms):
+        for inplace in (False, True):
+            for off in (0, 5):
+                n = W * H * C
+                cov = rng.integers(0, 256, n, dtype=np.uint8)
+                cap = (W // 4) * H
+                N = int(rng.integers(0, cap + 1)) if cap else 0
+                if gi == 2 and inplace and off == 0:
+                    N = cap + 1  # capacity error for this cover only
+                msg = rng.integers(0, 256, N, dtype=np.uint8)
+                gc = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+                cv = gc[off:off + n]
+                cv.copy_(torch.from_numpy(cov).cuda())
+                sv = cv if inplace else torch.full((n + 16,), 0x5A, dtype=torch.uint8,
+                                                   device="cuda")[off % 16:off % 16 + n]
+                mv = torch.from_numpy(msg).cuda()
+                keep += [gc, sv, mv]
+                recs.append(dict(cover=cv, stego=sv, msg=mv, cover_bytes=n, msg_bytes=N,
+                                 flags=S.LAYOUT_PAPER2, width=W, height=H, channels=C, plane=pl))
+                st, w = O.paper2_embed(cov, W, H, C, pl, msg)
+                want.append((st, w, cov, msg, sv, (W, H, C, pl)))
+    # a few stream-layout covers in the same batch
+    for C in (100, 4096, 70001):
+        cov = rng.integers(0, 256, C, dtype=np.uint8)
+        msg = rng.integers(0, 256, C // 8 - 4, dtype=np.uint8)
+        cv = torch.from_numpy(cov).cuda()
+        sv = torch.empty_like(cv)
+        mv = torch.from_numpy(msg).cuda()
+        keep += [cv, sv, mv]
+        recs.append(dict(cover=cv, stego=sv, msg=mv, cover_bytes=C, msg_bytes=msg.size,
+                         flags=S.HEADER_BE32))
+        st, w = O.stream1_embed(cov, msg, header=True)
+        want.append((st, w, cov, msg, sv, None))
+    n = len(recs)
+    for tile in (4096, 65536):
+        descs = S.descs_to_device(S.pack_descs(recs))
+        res = S.new_result(n=n)
+        ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        # in-place covers are rewritten by the first pass: restore them
+        for i, r in enumerate(recs):
+            if r["cover"].data_ptr() == r["stego"].data_ptr():
+                r["cover"].copy_(torch.from_numpy(want[i][2]).cuda())
+        S.stego_embed_batched(descs, n, res, S.FUSE_STATS, ws, tune=(256, 4, 0, tile))
+        rr = S.read_result(res)
+        for i, (st, w, cov, msg, sv, g) in enumerate(want):
+            assert rr[i]["status"] == st, (i, g, rr[i])
+            if st != 0:
+                continue
+            assert np.array_equal(sv.cpu().numpy(), w), (i, g, tile)
+            assert (rr[i]["changed"], rr[i]["sse"]) == O.changed_bytes(cov, w), (i, g)
+    # batched extraction (paper covers with their out-of-band length)
+    xr, xwant = [], []
+    for i, (st, w, cov, msg, sv, g) in enumerate(want):
+        if st != 0:
+            continue
+        out = torch.full((msg.size + 3,), 0xEE, dtype=torch.uint8, device="cuda")
+        keep.append(out)
+        if g is None:
+            xr.append(dict(cover=sv, msg=out, cover_bytes=cov.size, msg_bytes=out.numel(),
+                           flags=S.HEADER_BE32))
+        else:
+            W, H, C, pl = g
+            xr.append(dict(cover=sv, msg=out, cover_bytes=cov.size, msg_bytes=out.numel(),
+                           msg_len=msg.size, flags=S.LAYOUT_PAPER2, width=W, height=H,
+                           channels=C, plane=pl))
+        xwant.append((msg, out))
+    descs = S.descs_to_device(S.pack_descs(xr))
+    res = S.new_result(n=len(xr))
+    ws = torch.empty(S.stego_batched_workspace_bytes(len(xr)), dtype=torch.uint8, device="cuda")
+    S.stego_extract_batched(descs, len(xr), res, 0, ws)
+    rr = S.read_result(res)
+    for j, (msg, out) in enumerate(xwant):
+        assert rr[j]["status"] == 0 and rr[j]["msg_bytes"] == msg.size, (j, rr[j])
+        o = out.cpu().numpy()
+        assert np.array_equal(o[: msg.size], msg) and np.all(o[msg.size:] == 0xEE), j
+
+
+def test_batched_paper_layout_video(S, O):
+    """60 video frames (1920x1080x3) carrying the message stream in the
+    paper's layout (plane 0, 2 bits per byte, 388,796 bytes per frame), one
+    batched launch; sampled frames against the oracle, every frame's round
+    trip on the device."""
+    v = synth.Video(frames=60)
+    F, fb, P = v.frames, v.frame_bytes, v.per_frame_msg
+    frames = v.frame_range(0, F, "cuda").view(F, fb)
+    stream = v.message("cuda")
+    stego = torch.empty_like(frames)
+    geo = dict(width=v.width, height=v.height, channels=3, plane=0)
+    recs = [dict(cover=frames[f], stego=stego[f], msg=stream[f * P:(f + 1) * P], cover_bytes=fb,
+                 msg_bytes=P, flags=S.LAYOUT_PAPER2, **geo) for f in range(F)]
+    descs = S.descs_to_device(S.pack_descs(recs))
+    res = S.new_result(n=F)
+    ws = torch.empty(S.stego_batched_workspace_bytes(F), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(descs, F, res, S.FUSE_STATS, ws)
+    rr = S.read_result(res)
+    assert all(r["status"] == 0 and r["msg_bytes"] == P for r in rr)
+    for f in (0, 29, 59):
+        c = frames[f].cpu().numpy()
+        st, want = O.paper2_embed(c, v.width, v.height, 3, 0, stream[f * P:(f + 1) * P].cpu().numpy())
+        assert st == 0 and np.array_equal(stego[f].cpu().numpy(), want), f
+        assert (rr[f]["changed"], rr[f]["sse"]) == O.changed_bytes(c, want)
+    # the single-image one-pass kernel gives the same frame
+    one = torch.empty(fb, dtype=torch.uint8, device="cuda")
+    S.stego_embed(frames[7], one, stream[7 * P:8 * P], S.LAYOUT_PAPER2,
+                  geom=(v.width, v.height, 3, 0))
+    assert torch.equal(one, stego[7])
+    out = torch.empty(F * P, dtype=torch.uint8, device="cuda")
+    recs = [dict(cover=stego[f], msg=out[f * P:(f + 1) * P], cover_bytes=fb, msg_bytes=P,
+                 msg_len=P, flags=S.LAYOUT_PAPER2, **geo) for f in range(F)]
+    descs = S.descs_to_device(S.pack_descs(recs))
+    S.stego_extract_batched(descs, F, res, 0, ws)
+    assert torch.equal(out, stream)
