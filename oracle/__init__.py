@@ -78,6 +78,13 @@ class Oracle:
         lib.oracle_paper2_embed.restype = ctypes.c_int
         lib.oracle_paper2_extract.argtypes = [_u8p, _u32, _u32, _u32, _u32, _u8p, _u64, _u64]
         lib.oracle_paper2_extract.restype = ctypes.c_int
+        lib.oracle_streamk_embed.argtypes = [_u8p, _u8p, _u64, _u32, ctypes.c_int, _u32, _u32,
+                                             _u32, _u32, _u8p, _u64, ctypes.c_int]
+        lib.oracle_streamk_embed.restype = ctypes.c_int
+        lib.oracle_streamk_extract.argtypes = [_u8p, _u64, _u32, ctypes.c_int, _u32, _u32, _u32,
+                                               _u32, _u8p, _u64, ctypes.c_int, _u64,
+                                               ctypes.POINTER(_u64)]
+        lib.oracle_streamk_extract.restype = ctypes.c_int
         lib.oracle_changed_bytes.argtypes = [_u8p, _u8p, _u64, ctypes.POINTER(_u64),
                                              ctypes.POINTER(_u64)]
         lib.oracle_changed_bytes.restype = None
@@ -113,6 +120,31 @@ class Oracle:
         n = _u64(0)
         st = self.lib.oracle_stream1_extract(_ptr(stego), stego.size, _ptr(msg), int(cap),
                                              int(bool(header)), int(raw_len), ctypes.byref(n))
+        return st, msg[: n.value].copy()
+
+    # -- streamk: k bits per carrying byte, all bytes or one plane ---------
+    def streamk_embed(self, cover, msg, k, header=True, geom=None, out=None):
+        """geom=(W, H, channels, plane) selects one plane (plane_only)."""
+        cover = np.ascontiguousarray(cover, dtype=np.uint8).reshape(-1)
+        msg = np.ascontiguousarray(msg, dtype=np.uint8).reshape(-1)
+        if out is None:
+            out = np.zeros_like(cover)
+        W, H, C, p = geom if geom is not None else (0, 0, 0, 0)
+        st = self.lib.oracle_streamk_embed(_ptr(cover), _ptr(out), cover.size, int(k),
+                                           int(geom is not None), W, H, C, p, _ptr(msg),
+                                           msg.size, int(bool(header)))
+        return st, out
+
+    def streamk_extract(self, stego, k, cap=None, header=True, raw_len=0, geom=None):
+        stego = np.ascontiguousarray(stego, dtype=np.uint8).reshape(-1)
+        if cap is None:
+            cap = stego.size // 2 + 1
+        msg = np.full(max(int(cap), 1), STALE, dtype=np.uint8)
+        n = _u64(0)
+        W, H, C, p = geom if geom is not None else (0, 0, 0, 0)
+        st = self.lib.oracle_streamk_extract(_ptr(stego), stego.size, int(k), int(geom is not None),
+                                             W, H, C, p, _ptr(msg), int(cap), int(bool(header)),
+                                             int(raw_len), ctypes.byref(n))
         return st, msg[: n.value].copy()
 
     # -- paper2 ----------------------------------------------------------

@@ -21,6 +21,10 @@
  *    laid out sequentially; the length travels in a 32-bit big-endian bit-count
  *    header.
  *
+ *  - "streamk": the same stream with k = 1..4 bits per carrying byte, the
+ *    carrying bytes being every byte or, as in Section VI step 2, one colour
+ *    plane in pixel order (k = 1 over all bytes is "stream1").
+ *
  *  - "paper2": the literal algorithm of Section VI (embedding) and Section VII
  *    (extraction): one colour plane, two bits per cover byte, the message
  *    divided greedily among image rows with floor(W/4) bytes per row, and the
@@ -141,6 +145,132 @@ int oracle_stream1_extract(const uint8_t *st, uint64_t C, uint8_t *msg,
         uint8_t v = 0;
         for (b = 0; b < 8; ++b)
             v = (uint8_t)(v | ((st[base + 8u * s + (uint64_t)b] & 1u) << (7 - b)));
+        msg[s] = v;
+    }
+    if (out_len)
+        *out_len = len;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* streamk: k bits per carrying byte, all bytes or one plane                 */
+/* ------------------------------------------------------------------------ */
+
+/* The variant space between the one-bit stream and Section VI's two bits per
+ * byte (step 7c-f masks k = 2 low bits): k = 1..4 low bits of each carrying
+ * byte receive the next k stream bits, the first of them in the field's
+ * highest bit.  Stream bit b goes to bit (k - 1 - b mod k) of carrying byte
+ * b / k; when 8|S| is not a multiple of k, the last carrying byte changes
+ * only its top (8|S| mod k) field bits.  Carrying bytes are every cover byte
+ * in memory order (plane_only = 0) or, as in Section VI step 2, only the
+ * bytes of one colour plane in pixel order: carrying byte x is cover byte
+ * x*channels + plane. */
+
+static uint64_t carrying_index(uint64_t x, int plane_only, uint32_t Cch, uint32_t plane)
+{
+    return plane_only ? x * Cch + plane : x;
+}
+
+static int streamk_args_ok(uint64_t C, uint32_t k, int plane_only, uint32_t W, uint32_t H,
+                           uint32_t Cch, uint32_t plane)
+{
+    if (k < 1 || k > 4)
+        return 0;
+    if (plane_only && (Cch == 0 || plane >= Cch || (uint64_t)W * H * Cch != C))
+        return 0;
+    return 1;
+}
+
+/* Carrying bytes of the cover. */
+static uint64_t carrying_bytes(uint64_t C, int plane_only, uint32_t W, uint32_t H)
+{
+    return plane_only ? (uint64_t)W * H : C;
+}
+
+int oracle_streamk_embed(const uint8_t *cover, uint8_t *out, uint64_t C, uint32_t k,
+                         int plane_only, uint32_t W, uint32_t H, uint32_t Cch,
+                         uint32_t plane, const uint8_t *msg, uint64_t m, int header)
+{
+    uint64_t slen, nbits_stream, b;
+    if (!streamk_args_ok(C, k, plane_only, W, H, Cch, plane))
+        return OR_E_INVAL;
+    if (C > 0 && (cover == 0 || out == 0))
+        return OR_E_INVAL;
+    if (m > 0 && msg == 0)
+        return OR_E_INVAL;
+    if (header && m > OR_MAX_HEADER_MSG)
+        return OR_E_CAPACITY;
+    slen = m + (header ? 4u : 0u);
+    nbits_stream = 8u * slen;
+    /* the stream needs ceil(8|S| / k) carrying bytes */
+    if ((nbits_stream + k - 1) / k > carrying_bytes(C, plane_only, W, H))
+        return OR_E_CAPACITY;
+
+    if (out != cover)
+        memcpy(out, cover, (size_t)C);
+
+    for (b = 0; b < nbits_stream; ++b) {
+        uint8_t s = stream_byte(msg, m, header, b / 8u);
+        uint8_t bit = (uint8_t)((s >> (7u - (uint32_t)(b % 8u))) & 1u);
+        uint64_t x = carrying_index(b / k, plane_only, Cch, plane);
+        uint32_t pos = k - 1u - (uint32_t)(b % k);
+        out[x] = (uint8_t)((out[x] & ~(1u << pos)) | ((uint32_t)bit << pos));
+    }
+    return OR_OK;
+}
+
+/* Stream bit b read back from a stego. */
+static uint32_t streamk_bit(const uint8_t *st, uint64_t b, uint32_t k, int plane_only,
+                            uint32_t Cch, uint32_t plane)
+{
+    uint64_t x = carrying_index(b / k, plane_only, Cch, plane);
+    uint32_t pos = k - 1u - (uint32_t)(b % k);
+    return (st[x] >> pos) & 1u;
+}
+
+int oracle_streamk_extract(const uint8_t *st, uint64_t C, uint32_t k, int plane_only,
+                           uint32_t W, uint32_t H, uint32_t Cch, uint32_t plane, uint8_t *msg,
+                           uint64_t cap, int header, uint64_t raw_len, uint64_t *out_len)
+{
+    uint64_t avail_bits, len, first, s;
+    int i;
+    if (out_len)
+        *out_len = 0;
+    if (!streamk_args_ok(C, k, plane_only, W, H, Cch, plane))
+        return OR_E_INVAL;
+    if (C > 0 && st == 0)
+        return OR_E_INVAL;
+    avail_bits = (uint64_t)k * carrying_bytes(C, plane_only, W, H);
+    if (header) {
+        uint64_t nbits = 0, b;
+        if (avail_bits < 32u)
+            return OR_E_BAD_HEADER;
+        for (b = 0; b < 32u; ++b)
+            nbits |= (uint64_t)streamk_bit(st, b, k, plane_only, Cch, plane) << (31u - (uint32_t)b);
+        if (nbits % 8u != 0u)
+            return OR_E_BAD_HEADER;
+        if (32u + nbits > avail_bits)
+            return OR_E_BAD_HEADER;
+        len = nbits / 8u;
+        if (len > cap)
+            return OR_E_MSG_TOO_SMALL;
+        first = 32u;
+    } else {
+        len = raw_len;
+        if (8u * len > avail_bits)
+            return OR_E_CAPACITY;
+        if (len > cap)
+            return OR_E_MSG_TOO_SMALL;
+        first = 0u;
+    }
+    if (len > 0 && msg == 0)
+        return OR_E_INVAL;
+    for (s = 0; s < len; ++s) {
+        uint8_t v = 0;
+        for (i = 0; i < 8; ++i)
+            v = (uint8_t)(v | (streamk_bit(st, first + 8u * s + (uint64_t)i, k, plane_only, Cch,
+                                           plane)
+                               << (7 - i)));
         msg[s] = v;
     }
     if (out_len)

@@ -153,6 +153,19 @@ def check_golden(o: orc.Oracle, name: str):
     elif lay == "stream1-extract":
         st, m = o.stream1_extract(g["stego"], cap=64, header=bool(g["header"]))
         assert st == g["status"], (name, st)
+    elif lay == "streamk":
+        geom = (g["width"], g["height"], g["channels"], g["plane"]) if "width" in g else None
+        sentinel = np.full_like(g["cover"], 0x5A)
+        st, out = o.streamk_embed(g["cover"], g["msg"], g["k"], header=bool(g["header"]),
+                                  geom=geom, out=sentinel.copy())
+        assert st == g["status"], (name, st)
+        if st != orc.OK:
+            assert out.tolist() == sentinel.tolist()
+            return
+        assert out.tolist() == g["stego"].tolist(), (name, out)
+        st2, m = o.streamk_extract(out, g["k"], cap=len(g["msg"]), header=bool(g["header"]),
+                                   raw_len=len(g["msg"]), geom=geom)
+        assert st2 == orc.OK and m.tolist() == g["msg"].tolist(), name
     elif lay == "paper2":
         W, H, C, p = g["width"], g["height"], g["channels"], g["plane"]
         sentinel = np.full_like(g["cover"], 0x5A)
@@ -468,6 +481,132 @@ def pin_changed_definition(o):
     assert o.changed_bytes(a, b) == (2, 255 * 255 + 1)
 
 
+# --------------------------------------------------------------------------
+# k bits per carrying byte, all bytes or one plane
+# --------------------------------------------------------------------------
+
+def brute_streamk_embed(cover: bytes, msg: bytes, k: int, header: bool, geom=None):
+    bits = brute_stream_bits(msg, header)
+    if geom is None:
+        carry = list(range(len(cover)))
+    else:
+        W, H, C, p = geom
+        carry = [x * C + p for x in range(W * H)]
+    if -(-len(bits) // k) > len(carry):
+        return None
+    out = list(cover)
+    for x in range(0, len(bits), k):
+        field = bits[x:x + k]
+        pos = carry[x // k]
+        value = format(out[pos], "08b")           # bit 7 first
+        lo = list(value[8 - k:])                  # the k low bits, high first
+        lo[:len(field)] = [str(b) for b in field]
+        out[pos] = int(value[:8 - k] + "".join(lo), 2)
+    return bytes(out)
+
+
+def pin_golden_streamk_relation(o):
+    """k = 1 over all bytes is the one-bit stream layout."""
+    r = rng(21)
+    for C in (0, 40, 333, 4096):
+        cover = r.integers(0, 256, C, dtype=np.uint8)
+        for header in (True, False):
+            cap = max(C // 8 - (4 if header else 0), 0)
+            msg = r.integers(0, 256, cap, dtype=np.uint8)
+            a = o.stream1_embed(cover, msg, header=header)
+            b = o.streamk_embed(cover, msg, 1, header=header)
+            assert a[0] == b[0] and np.array_equal(a[1], b[1]), (C, header)
+
+
+def pin_table_streamk(o):
+    """Every cover byte value with every k-bit field, k = 2, 3, 4: eight
+    carrying bytes all get (c & ~(2^k - 1)) | f."""
+    for k in (2, 3, 4):
+        for f in range(1 << k):
+            bits = format(f, "0%db" % k) * 8       # eight fields
+            msg = np.array([int(bits[i:i + 8], 2) for i in range(0, 8 * k, 8)], np.uint8)
+            for c in range(256):
+                st, out = o.streamk_embed(np.full(8, c, np.uint8), msg, k, header=False)
+                assert st == orc.OK
+                want = (c - c % (1 << k)) + f
+                assert out.tolist() == [want] * 8, (k, f, c, out)
+
+
+def pin_brute_streamk(o):
+    r = rng(22)
+    for k in (1, 2, 3, 4):
+        for geom in (None, (3, 2, 3, 1), (5, 3, 1, 0), (4, 4, 4, 3), (2, 5, 2, 0)):
+            for C in ((0, 7, 31, 40, 64) if geom is None else (geom[0] * geom[1] * geom[2],)):
+                cover = r.integers(0, 256, C, dtype=np.uint8)
+                ncarry = C if geom is None else geom[0] * geom[1]
+                for header in (False, True):
+                    cap = max(k * ncarry // 8 - (4 if header else 0), 0)
+                    for m in sorted({0, 1, cap // 2, cap, cap + 1}):
+                        msg = r.integers(0, 256, m, dtype=np.uint8)
+                        want = brute_streamk_embed(bytes(cover), bytes(msg), k, header, geom)
+                        st, out = o.streamk_embed(cover, msg, k, header=header, geom=geom)
+                        if want is None:
+                            assert st == orc.E_CAPACITY, (k, geom, C, m, header, st)
+                            continue
+                        assert st == orc.OK and bytes(out) == want, (k, geom, C, m, header)
+                        st2, m2 = o.streamk_extract(out, k, cap=m, header=header, raw_len=m,
+                                                    geom=geom)
+                        assert st2 == orc.OK and bytes(m2) == bytes(msg), (k, geom, C, m)
+
+
+def pin_invariants_streamk(o):
+    r = rng(23)
+    for k in (2, 3, 4):
+        for geom in (None, (64, 9, 3, 2), (33, 7, 4, 0)):
+            C = 5000 if geom is None else geom[0] * geom[1] * geom[2]
+            cover = r.integers(0, 256, C, dtype=np.uint8)
+            ncarry = C if geom is None else geom[0] * geom[1]
+            cap = k * ncarry // 8 - 4
+            for m in (0, cap // 3, cap):
+                msg = r.integers(0, 256, m, dtype=np.uint8)
+                st, out = o.streamk_embed(cover, msg, k, header=True, geom=geom)
+                assert st == orc.OK
+                d = out.astype(np.int16) - cover.astype(np.int16)
+                assert np.all(np.abs(d) < (1 << k))
+                assert np.all(((out ^ cover) & (0xFF ^ ((1 << k) - 1))) == 0)
+                T = -(-8 * (m + 4) // k)  # carrying bytes used
+                if geom is None:
+                    assert np.array_equal(out[T:], cover[T:])
+                else:
+                    W, H, Cc, p = geom
+                    mask = np.ones(C, bool)
+                    mask[np.arange(T) * Cc + p] = False
+                    assert np.array_equal(out[mask], cover[mask])
+                st2, m2 = o.streamk_extract(out, k, cap=m, header=True, geom=geom)
+                assert st2 == orc.OK and np.array_equal(m2, msg)
+
+
+def pin_errors_streamk(o):
+    c = np.zeros(64, np.uint8)
+    assert o.streamk_embed(c, np.zeros(1, np.uint8), 0, header=False)[0] == orc.E_INVAL
+    assert o.streamk_embed(c, np.zeros(1, np.uint8), 5, header=False)[0] == orc.E_INVAL
+    assert o.streamk_embed(c, np.zeros(1, np.uint8), 2, header=False,
+                           geom=(8, 8, 1, 1))[0] == orc.E_INVAL          # plane >= channels
+    assert o.streamk_embed(c, np.zeros(1, np.uint8), 2, header=False,
+                           geom=(8, 4, 3, 0))[0] == orc.E_INVAL          # size mismatch
+    # 64 bytes x 3 bits = 192 bits = 24 bytes: 20 message bytes behind the header
+    assert o.streamk_embed(c, np.zeros(20, np.uint8), 3, header=True)[0] == orc.OK
+    assert o.streamk_embed(c, np.zeros(21, np.uint8), 3, header=True)[0] == orc.E_CAPACITY
+    # k = 2: header bits 28..31 sit in carrying bytes 14 and 15; a count of 9
+    # bits (fields 2, 1) fits 64 bytes but is not whole bytes; 8 (fields 2, 0)
+    # is one message byte
+    h9 = np.zeros(64, np.uint8)
+    h9[14], h9[15] = 2, 1
+    assert o.streamk_extract(h9, 2, cap=8, header=True)[0] == orc.E_BAD_HEADER
+    h8 = np.zeros(64, np.uint8)
+    h8[14] = 2
+    st, m = o.streamk_extract(h8, 2, cap=8, header=True)
+    assert st == orc.OK and m.size == 1
+    # a header needs 32 stream bits: 10 bytes at k = 3 (30 bits) are too few
+    assert o.streamk_extract(np.zeros(10, np.uint8), 3, header=True)[0] == orc.E_BAD_HEADER
+    assert o.streamk_extract(np.zeros(11, np.uint8), 3, header=True)[0] == orc.OK
+
+
 PINS = [
     ("golden", pin_golden),
     ("table_stream1", pin_table_stream1),
@@ -481,4 +620,9 @@ PINS = [
     ("section8_session", pin_section8_session),
     ("psnr_gap", pin_psnr_gap),
     ("changed_definition", pin_changed_definition),
+    ("streamk_k1_is_stream1", pin_golden_streamk_relation),
+    ("table_streamk", pin_table_streamk),
+    ("brute_streamk", pin_brute_streamk),
+    ("invariants_streamk", pin_invariants_streamk),
+    ("errors_streamk", pin_errors_streamk),
 ]

@@ -45,6 +45,16 @@ MUTANTS = [
     ("paper_extract_mask1", "(st[x] & 0x03u)", "(st[x] & 0x01u)", 1),
     ("paper_extract_shift_i", "y = (uint8_t)(y << (2 * i));", "y = (uint8_t)(y << i);", 1),
     ("paper_extract_no_zero", "msg[off + j] = 0;", "(void)0;", 1),
+    # streamk
+    ("streamk_field_lsb_first", "uint32_t pos = k - 1u - (uint32_t)(b % k);\n        out[x]",
+     "uint32_t pos = (uint32_t)(b % k);\n        out[x]", 1),
+    ("streamk_extract_field_order", "uint32_t pos = k - 1u - (uint32_t)(b % k);\n    return",
+     "uint32_t pos = (uint32_t)(b % k);\n    return", 1),
+    ("streamk_plane_ignored", "return plane_only ? x * Cch + plane : x;",
+     "return plane_only ? x * Cch : x;", 1),
+    ("streamk_header_no_byte_check", "if (nbits % 8u != 0u)", "if (0)", 2),
+    ("streamk_clear_whole_field", "out[x] = (uint8_t)((out[x] & ~(1u << pos)) | ((uint32_t)bit << pos));",
+     "out[x] = (uint8_t)((out[x] & ~((1u << k) - 1u) & 0xFFu) | ((uint32_t)bit << pos) | (out[x] & ((1u << pos) - 1u)));", 1),
     # statistics
     ("changed_positive_only", "if (d != 0)", "if (d > 0)", 1),
     ("sse_abs", "s += (uint64_t)(d * d);", "s += (uint64_t)(d < 0 ? -d : d);", 1),
@@ -69,15 +79,25 @@ def test_unmutated_passes_all(oracle_lib):
     assert _first_failure(oracle_lib) is None
 
 
-@pytest.mark.parametrize("mname,find,repl,count", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(workdir, mname, find, repl, count):
+def _replace_nth(src, find, repl, nth):
+    """Replace the nth (1-based) occurrence of find."""
+    at = -1
+    for _ in range(nth):
+        at = src.find(find, at + 1)
+        assert at >= 0
+    return src[:at] + repl + src[at + len(find):]
+
+
+@pytest.mark.parametrize("mname,find,repl,nth", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(workdir, mname, find, repl, nth):
+    """nth: which occurrence of `find` in the oracle source is mutated."""
     with open(os.path.join(os.path.dirname(oracle.__file__), "stego_oracle.c")) as f:
         src = f.read()
-    assert src.count(find) == count, "mutation site not found: " + mname
+    assert src.count(find) >= nth, "mutation site not found: " + mname
     mdir = workdir / mname
     mdir.mkdir()
     path = mdir / "m.c"
-    path.write_text(src.replace(find, repl))
+    path.write_text(_replace_nth(src, find, repl, nth))
     lib = oracle.build(str(path), str(mdir / "libm.so"))
     o = oracle.Oracle(lib)
     caught = _first_failure(o)
