@@ -80,6 +80,19 @@ enum stego_status {
 #define STEGO_LAYOUT_MASK 0xFu
 #define STEGO_HEADER_BE32 0x10u /* STREAM1 only: 32-bit big-endian bit count */
 #define STEGO_FUSE_STATS 0x20u  /* embed: count changed bytes and SSE      */
+/* STREAM1 variants between one bit per byte and Section VI's two:
+ *   STEGO_BITS(k), k = 1..4: k low bits of every carrying byte take the next
+ *   k stream bits, the first in the field's highest bit (stream bit b goes to
+ *   bit k-1-(b mod k) of carrying byte b/k); when 8|S| is not a multiple of
+ *   k the last carrying byte changes only its top (8|S| mod k) field bits.
+ *   STEGO_PLANE_ONLY: the carrying bytes are the bytes of channel
+ *   geom->plane in pixel order (Section VI step 2), carrying byte x being
+ *   cover byte x*channels + plane; geom is then required.
+ * Without either flag STREAM1 is one bit over every byte in memory order.
+ * The batched and serving calls take the default (one bit, all bytes). */
+#define STEGO_PLANE_ONLY 0x40u
+#define STEGO_BITS_MASK 0x300u
+#define STEGO_BITS(k) ((((uint32_t)(k)) - 1u) << 8)
 
 /* Image geometry for STEGO_LAYOUT_PAPER2: `height` rows of `width` pixels
  * with `channels` interleaved uint8 channels; the message goes into channel
@@ -161,12 +174,15 @@ int stego_version(void);
 const char *stego_strerror(int status);
 
 /* Largest message (bytes) that fits a cover of `cover_bytes`:
- *   STREAM1 with header: floor(C/8) - 4 (at least 0, at most 2^29 - 1;
- *                        a cover under 32 bytes cannot hold the header, so
- *                        even an empty message is STEGO_E_CAPACITY there);
- *   STREAM1 raw:        floor(C/8);
+ *   STREAM1 with header: floor(k*Cc/8) - 4 (at least 0, at most 2^29 - 1;
+ *                        Cc = carrying bytes: cover_bytes, or width*height
+ *                        with STEGO_PLANE_ONLY; a cover whose k*Cc is under
+ *                        32 bits cannot hold the header, so even an empty
+ *                        message is STEGO_E_CAPACITY there);
+ *   STREAM1 raw:        floor(k*Cc/8);
  *   PAPER2:             floor(W/4) * H   (Section VI step 5: 4*|B| <= |A|).
- * geom is required for PAPER2 and ignored otherwise.  Writes *out_msg_bytes.
+ * geom is required for PAPER2 and STEGO_PLANE_ONLY and ignored otherwise.
+ * Writes *out_msg_bytes.
  * Returns STEGO_OK or STEGO_E_INVAL. */
 int stego_capacity(uint64_t cover_bytes, const stego_geom *geom, uint32_t flags,
                    uint64_t *out_msg_bytes);

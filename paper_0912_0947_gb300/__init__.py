@@ -24,6 +24,14 @@ LAYOUT_STREAM1 = 0x0
 LAYOUT_PAPER2 = 0x1
 HEADER_BE32 = 0x10
 FUSE_STATS = 0x20
+PLANE_ONLY = 0x40   # stream layout: carry only in channel geom.plane, pixel order
+
+
+def BITS(k: int) -> int:
+    """Stream-layout flag for k = 1..4 bits per carrying byte."""
+    if not 1 <= k <= 4:
+        raise ValueError("k must be 1..4")
+    return (k - 1) << 8
 
 OK = 0
 E_INVAL = -1

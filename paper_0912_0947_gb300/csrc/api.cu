@@ -87,6 +87,15 @@ __global__ void write_result_kernel(stego_result *res, uint64_t msg_bytes, int s
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? STEGO_OK : STEGO_E_CUDA; }
 
+// An image geometry that describes exactly cover_bytes bytes.
+bool geom_ok(const stego_geom *g, uint64_t cover_bytes)
+{
+    return g && g->channels > 0 && g->plane < g->channels &&
+           (uint64_t)g->width * g->height * g->channels == cover_bytes;
+}
+
+uint32_t bits_of(uint32_t flags) { return ((flags & STEGO_BITS_MASK) >> 8) + 1u; }
+
 } // namespace
 
 bool tune_ok(const stego_tune *t) { return t && valid_tune_field_ranges(*t); }
@@ -175,7 +184,14 @@ int stego_capacity(uint64_t cover_bytes, const stego_geom *geom, uint32_t flags,
         return STEGO_E_INVAL;
     const uint32_t layout = flags & STEGO_LAYOUT_MASK;
     if (layout == STEGO_LAYOUT_STREAM1) {
-        uint64_t cap = cover_bytes / 8u;
+        const uint32_t k = ((flags & STEGO_BITS_MASK) >> 8) + 1u;
+        uint64_t carry = cover_bytes;
+        if (flags & STEGO_PLANE_ONLY) {
+            if (!geom_ok(geom, cover_bytes))
+                return STEGO_E_INVAL;
+            carry = (uint64_t)geom->width * geom->height;
+        }
+        uint64_t cap = carry * k / 8u;
         if (flags & STEGO_HEADER_BE32) {
             cap = cap >= 4u ? cap - 4u : 0u;
             if (cap > kMaxHeaderMsg)
@@ -185,8 +201,7 @@ int stego_capacity(uint64_t cover_bytes, const stego_geom *geom, uint32_t flags,
         return STEGO_OK;
     }
     if (layout == STEGO_LAYOUT_PAPER2) {
-        if (!geom || geom->channels == 0 || geom->plane >= geom->channels ||
-            (uint64_t)geom->width * geom->height * geom->channels != cover_bytes)
+        if (!geom_ok(geom, cover_bytes))
             return STEGO_E_INVAL;
         *out_msg_bytes = (uint64_t)(geom->width / 4u) * geom->height;
         return STEGO_OK;
@@ -198,15 +213,18 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
                 const uint8_t *d_msg, uint64_t msg_bytes, const stego_geom *geom,
                 uint32_t flags, stego_result *d_result, void *stream)
 {
-    const uint32_t known = STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS;
+    const uint32_t known = STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS |
+                           STEGO_PLANE_ONLY | STEGO_BITS_MASK;
     if (flags & ~known)
         return STEGO_E_INVAL;
     const uint32_t layout = flags & STEGO_LAYOUT_MASK;
     const bool header = (flags & STEGO_HEADER_BE32) != 0;
     const bool stats = (flags & STEGO_FUSE_STATS) != 0;
+    const bool plane_only = (flags & STEGO_PLANE_ONLY) != 0;
+    const uint32_t k = bits_of(flags);
     if (layout != STEGO_LAYOUT_STREAM1 && layout != STEGO_LAYOUT_PAPER2)
         return STEGO_E_INVAL;
-    if (layout == STEGO_LAYOUT_PAPER2 && header)
+    if (layout == STEGO_LAYOUT_PAPER2 && (header || plane_only || k != 1))
         return STEGO_E_INVAL;
     if (cover_bytes > 0 && (!d_cover || !d_stego))
         return STEGO_E_INVAL;
@@ -231,14 +249,27 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
         return st;
     if (msg_bytes > cap)
         return STEGO_E_CAPACITY;
-    if (layout == STEGO_LAYOUT_STREAM1 && header && cover_bytes < 32)
-        return STEGO_E_CAPACITY; // the header alone needs 32 cover bytes
+    if (layout == STEGO_LAYOUT_STREAM1 && header) {
+        // the header alone needs 32 stream bits
+        const uint64_t carry = plane_only ? (uint64_t)geom->width * geom->height : cover_bytes;
+        if (carry * k < 32u)
+            return STEGO_E_CAPACITY;
+    }
 
     cudaStream_t s = (cudaStream_t)stream;
     const Shape sh = shape_for(STEGO_OP_EMBED, nullptr);
     if (stats && cudaMemsetAsync(d_result, 0, 2 * sizeof(uint64_t), s) != cudaSuccess)
         return STEGO_E_CUDA;
 
+    if (layout == STEGO_LAYOUT_STREAM1 && (k != 1 || plane_only)) {
+        if (cover_bytes == 0 || (!header && msg_bytes == 0 && inplace)) {
+            if (d_result)
+                return cuda_status(write_result(d_result, msg_bytes, STEGO_OK, s));
+            return STEGO_OK;
+        }
+        return cuda_status(sk_embed(d_cover, d_stego, cover_bytes, k, plane_only, geom, d_msg,
+                                    msg_bytes, header, stats, d_result, sh, s));
+    }
     if (layout == STEGO_LAYOUT_STREAM1) {
         const uint64_t slen = msg_bytes + (header ? 4u : 0u);
         const uint64_t T = 8u * slen;
@@ -276,14 +307,19 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
                   uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom, uint32_t flags,
                   stego_result *d_result, void *stream)
 {
-    const uint32_t known = STEGO_LAYOUT_MASK | STEGO_HEADER_BE32;
+    const uint32_t known = STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_PLANE_ONLY |
+                           STEGO_BITS_MASK;
     if (flags & ~known)
         return STEGO_E_INVAL;
     const uint32_t layout = flags & STEGO_LAYOUT_MASK;
     const bool header = (flags & STEGO_HEADER_BE32) != 0;
+    const bool plane_only = (flags & STEGO_PLANE_ONLY) != 0;
+    const uint32_t k = bits_of(flags);
     if (layout != STEGO_LAYOUT_STREAM1 && layout != STEGO_LAYOUT_PAPER2)
         return STEGO_E_INVAL;
-    if (layout == STEGO_LAYOUT_PAPER2 && header)
+    if (layout == STEGO_LAYOUT_PAPER2 && (header || plane_only || k != 1))
+        return STEGO_E_INVAL;
+    if (plane_only && !geom_ok(geom, cover_bytes))
         return STEGO_E_INVAL;
     if (cover_bytes > 0 && !d_stego)
         return STEGO_E_INVAL;
@@ -301,8 +337,12 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
     cudaStream_t s = (cudaStream_t)stream;
     const Shape sh = shape_for(STEGO_OP_EXTRACT, nullptr);
 
+    const bool variant = layout == STEGO_LAYOUT_STREAM1 && (k != 1 || plane_only);
     if (layout == STEGO_LAYOUT_STREAM1 && header) {
         // length and status come from the device
+        if (variant)
+            return cuda_status(sk_extract(d_stego, cover_bytes, k, plane_only, geom, d_msg,
+                                          msg_cap, 0, true, d_result, sh, s));
         return cuda_status(s1_extract(d_stego, cover_bytes, d_msg, msg_cap, 0, true, d_result, sh, s));
     }
     uint64_t cap = 0;
@@ -318,6 +358,9 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
             return cuda_status(write_result(d_result, 0, STEGO_OK, s));
         return STEGO_OK;
     }
+    if (variant)
+        return cuda_status(sk_extract(d_stego, cover_bytes, k, plane_only, geom, d_msg, msg_cap,
+                                      msg_len, false, d_result, sh, s));
     if (layout == STEGO_LAYOUT_STREAM1)
         return cuda_status(s1_extract(d_stego, cover_bytes, d_msg, msg_cap, msg_len, false, d_result, sh, s));
     return cuda_status(p2_extract(d_stego, *geom, d_msg, msg_len, d_result, sh, s));

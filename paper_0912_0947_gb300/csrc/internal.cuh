@@ -73,6 +73,15 @@ cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geo
                            const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
                            const Shape &sh, cudaStream_t s);
 
+// STREAM1 with k = 1..4 bits per carrying byte, over all bytes or one plane
+// (k >= 2 or plane_only; k = 1 over all bytes is s1_embed).
+cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t k, bool plane_only,
+                     const stego_geom *g, const uint8_t *msg, uint64_t m, bool header,
+                     bool stats, stego_result *res, const Shape &sh, cudaStream_t s);
+cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_only,
+                       const stego_geom *g, uint8_t *msg, uint64_t cap, uint64_t raw_len,
+                       bool header, stego_result *res, const Shape &sh, cudaStream_t s);
+
 // Changed-byte count and SSE of two arrays into out2[0..1] (zeroed by the
 // caller).
 cudaError_t changed_bytes(const uint8_t *a, const uint8_t *b, uint64_t n,
