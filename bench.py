@@ -4,9 +4,10 @@ cover (201,326,592 bytes) carrying a message at full one-bit capacity
 (25,165,820 bytes behind the 32-bit header).
 
 One step = one embed (with the fused changed-byte/SSE count) and one
-extract of that cover, inputs resident in HBM.  L2 (129 MB) is flushed by a
-256 MiB memset before each timed kernel; the flushes sit outside the timed
-intervals, which CUDA events on the launching stream measure.
+extract of that cover, inputs resident in HBM.  The L2 (129 MB) is flushed
+before each timed call (a 256 MiB write, then a 512 MiB read so no dirty
+line is left); the flushes sit outside the timed intervals, which CUDA
+events on the launching stream measure.
 value = cover bytes processed (2 per step: the embed and the extract each
 traverse the cover once) / device time, summed over ranks for N > 1 (each
 rank runs its own replica; no data-path collective).
@@ -224,9 +225,9 @@ def run_ours(args, rank, world, local_rank):
     legs = {}
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
                                                          "batched_video_paper2", "paper2",
-                                                         "serving"}
+                                                         "streamk", "serving"}
     if args.no_batched:
-        want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2"}
+        want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk"}
     if args.no_serving:
         want.discard("serving")
     del flush
@@ -238,6 +239,9 @@ def run_ours(args, rank, world, local_rank):
                 count=(args.uneven_count if kind == "uneven" else args.video_frames) or None,
                 tune=not args.no_tune)
             torch.cuda.empty_cache()
+    if rank == 0 and "streamk" in want:
+        legs["streamk"] = run_streamk_leg(S, AT, torch, dev, synth)
+        torch.cuda.empty_cache()
     if rank == 0 and "paper2" in want:
         legs["paper2"] = run_paper2_leg(S, AT, torch, dev, synth)
         torch.cuda.empty_cache()
@@ -272,7 +276,8 @@ def run_ours(args, rank, world, local_rank):
                         "(25165820 B message + 32-bit header); embed (fused stats) + extract",
             "cover_bytes": C, "msg_bytes": m, "carrying_bytes": T,
             "l2": "flushed before each timed call, outside the timed interval: write 256 MiB, "
-                  "then read another 256 MiB so no dirty line is left for the timed call",
+                  "then read 512 MiB so no dirty line is left for the timed call, then a "
+                  "100k-cycle GPU spin so the call is queued before its start event runs",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "launch": {"embed": tune_dict(S.stego_get_tune(S.OP_EMBED)),
                        "extract": tune_dict(S.stego_get_tune(S.OP_EXTRACT))},
@@ -569,6 +574,48 @@ def run_paper2_leg(S, AT, torch, dev, synth):
         "algorithmic_bytes": {"embed_out_of_place": 2 * C + N, "embed_in_place": 9 * N,
                               "extract": 5 * N},
     }
+
+
+def run_streamk_leg(S, AT, torch, dev, synth):
+    """The stream layout with k bits per carrying byte on the 8192x8192x3
+    cover at full capacity: k = 2 and 4 over all bytes (algorithmic bytes
+    2C + 8|S|/8 embed, C + |S| extract) and k = 2 on plane 0 (carrying bytes
+    every third byte: sectors of the whole cover move)."""
+    C = 8192 * 8192 * 3
+    cover = synth.uniform_bytes(C, synth.substream(synth.SEED_BASE + 7, 1), dev)
+    stego = torch.empty_like(cover)
+    res = S.new_result(dev)
+    flush = AT.Flusher(dev)
+    peak, _ = hbm_peak()
+    out = {}
+    for name, k, geom in (("k2_all", 2, None), ("k4_all", 4, None),
+                          ("k2_plane0", 2, (8192, 8192, 3, 0))):
+        flags = S.BITS(k) | S.HEADER_BE32 | (S.PLANE_ONLY if geom else 0)
+        m = S.stego_capacity(C, flags, geom=geom)
+        msg = synth.uniform_bytes(m, synth.substream(synth.SEED_BASE + 7, 10 + k), dev)
+        got = torch.empty(m, dtype=torch.uint8, device=dev)
+
+        def emb():
+            S.stego_embed(cover, stego, msg, flags | S.FUSE_STATS, res, geom=geom)
+
+        def ext():
+            S.stego_extract(stego, got, 0, flags, res, geom=geom)
+
+        te = AT.time_call(emb, flush, 15)
+        tx = AT.time_call(ext, flush, 15)
+        torch.cuda.synchronize()
+        assert torch.equal(got, msg)
+        s_bytes = m + 4
+        carry = -(-8 * s_bytes // k) * (3 if geom else 1)  # cover bytes spanned by the carriers
+        eb = 2 * C + s_bytes
+        xb = min(carry, C) + s_bytes
+        out[name] = {"msg_bytes": m, "embed_us": round(te, 2), "extract_us": round(tx, 2),
+                     "embed_cover_gbs": round(C / (te * 1e-6) / 1e9, 1),
+                     "extract_cover_gbs": round(C / (tx * 1e-6) / 1e9, 1),
+                     "embed_hbm_frac": round(eb / (te * 1e-6) / 1e9 / peak, 4),
+                     "extract_hbm_frac": round(xb / (tx * 1e-6) / 1e9 / peak, 4)}
+        del msg, got
+    return out
 
 
 def tune_dict(t):

@@ -71,18 +71,31 @@ def _store(op: int, size_bytes: int, shape, us: float, device=None) -> None:
         pass
 
 
+# GPU cycles the flush ends with (about 50 us at 2 GHz): the host enqueues
+# the timed call while the GPU still spins, so the call's start event never
+# waits on host-side launch latency.
+SPIN_CYCLES = 100_000
+
+
 class Flusher:
     """Evicts the L2 between timed repetitions: writes a buffer larger than
-    the L2, then reads another one so the written lines are cleaned before
-    the timed call (a dirty L2 would charge its write-back to that call)."""
+    the L2 (129 MB), then reads a buffer twice that size so the written lines
+    are written back before the timed call (a 256 MiB read after the 256 MiB
+    write still left dirty lines whose write-back added ~2 us to a 201 MB
+    extract; 512 MiB gives the same time as a read-only flush), then spins
+    briefly on the GPU so the timed call is already queued when its start
+    event executes."""
 
-    def __init__(self, device, nbytes: int = L2_FLUSH_BYTES):
+    def __init__(self, device, nbytes: int = L2_FLUSH_BYTES, spin_cycles: int = SPIN_CYCLES):
         self.a = torch.empty(nbytes, dtype=torch.uint8, device=device)
-        self.b = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+        self.b = torch.zeros(2 * nbytes, dtype=torch.uint8, device=device)
+        self.spin = spin_cycles
 
     def __call__(self):
         self.a.fill_(1)
         self.b.view(torch.int32).max()  # a read-only pass, no temporary
+        if self.spin:
+            torch.cuda._sleep(self.spin)
 
 
 def time_call(fn, flush, reps: int = 15, stream=None) -> float:

@@ -118,9 +118,36 @@ __device__ __noinline__ uint4 stream_end_vector(const KView &a, uint64_t v, uint
     return make_uint4(ow[0], ow[1], ow[2], ow[3]);
 }
 
+// Stream bytes [2Kv, 2Kv + 2K) as a big-endian 64-bit word (whole vector
+// inside the stream): word loads when they are message bytes on a 4-byte
+// boundary, byte loads otherwise.
+template <int K>
+__device__ __forceinline__ uint64_t stream_window(const KView &a, uint64_t v)
+{
+    uint64_t X = 0;
+    const uint64_t q0 = 2u * K * v;
+    const uint64_t hb = a.header ? 4u : 0u;
+    const uint8_t *mp = a.msg + (q0 - hb);
+    if ((K & 1) == 0 && q0 >= hb && (((uintptr_t)mp & 3u) == 0)) {
+#pragma unroll
+        for (int i = 0; i < K / 2; ++i) {
+            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(mp) + i);
+            X |= (uint64_t)__byte_perm(w, 0u, 0x0123u) << (32 - 32 * i);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i)
+            X |= (uint64_t)sbyte(a, q0 + i) << (56 - 8 * i);
+    }
+    return X;
+}
+
+// Grid-stride over 16-byte vectors (V per thread per iteration, cover and
+// stream loads issued before any arithmetic).
 template <int K, bool STATS>
 __global__ void __launch_bounds__(512) embedk_vec(KView a)
 {
+    constexpr int V = 1; // more in flight measured slower (registers)
     constexpr uint32_t MASK = (1u << K) - 1u;
     constexpr uint32_t BYTEMASK = MASK * 0x01010101u;
     unsigned long long changed = 0, sse = 0;
@@ -128,40 +155,56 @@ __global__ void __launch_bounds__(512) embedk_vec(KView a)
     const uint64_t nvec = a.n_carry >> 4;
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover);
     uint4 *dst = reinterpret_cast<uint4 *>(a.stego);
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 c = __ldcs(src + v);
-        uint4 o = c;
-        const uint64_t b0 = v * 16u * K; // first stream bit of the vector
-        if (b0 + 16u * K <= a.t_bits) {
-            // whole vector carries: 2K stream bytes, big-endian, in X
-            uint64_t X = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * V;
+    for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x; v0 < nvec;
+         v0 += stride) {
+        uint4 c[V];
+        uint64_t X[V];
 #pragma unroll
-            for (int i = 0; i < 2 * K; ++i)
-                X |= (uint64_t)sbyte(a, 2u * K * v + i) << (56 - 8 * i);
-            uint32_t f[4];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                f[w] = 0;
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const int t = 4 * w + l;
-                    f[w] |= (uint32_t)((X >> (64 - K * (t + 1))) & MASK) << (8 * l);
-                }
-            }
-            o.x = (c.x & ~BYTEMASK) | f[0];
-            o.y = (c.y & ~BYTEMASK) | f[1];
-            o.z = (c.z & ~BYTEMASK) | f[2];
-            o.w = (c.w & ~BYTEMASK) | f[3];
-        } else if (b0 < a.t_bits) {
-            o = stream_end_vector(a, v, c);
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v < nvec)
+                c[u] = __ldcs(src + v);
         }
-        __stcs(dst + v, o);
-        if (STATS) {
-            low_stats(o.x, c.x, changed, sse);
-            low_stats(o.y, c.y, changed, sse);
-            low_stats(o.z, c.z, changed, sse);
-            low_stats(o.w, c.w, changed, sse);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            X[u] = 0;
+            if (v < nvec && (v + 1) * 16u * K <= a.t_bits)
+                X[u] = stream_window<K>(a, v);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v >= nvec)
+                continue;
+            uint4 o = c[u];
+            const uint64_t b0 = v * 16u * K; // first stream bit of the vector
+            if (b0 + 16u * K <= a.t_bits) {
+                uint32_t f[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    f[w] = 0;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const int t = 4 * w + l;
+                        f[w] |= (uint32_t)((X[u] >> (64 - K * (t + 1))) & MASK) << (8 * l);
+                    }
+                }
+                o.x = (c[u].x & ~BYTEMASK) | f[0];
+                o.y = (c[u].y & ~BYTEMASK) | f[1];
+                o.z = (c[u].z & ~BYTEMASK) | f[2];
+                o.w = (c[u].w & ~BYTEMASK) | f[3];
+            } else if (b0 < a.t_bits) {
+                o = stream_end_vector(a, v, c[u]);
+            }
+            __stcs(dst + v, o);
+            if (STATS) {
+                low_stats(o.x, c[u].x, changed, sse);
+                low_stats(o.y, c[u].y, changed, sse);
+                low_stats(o.z, c[u].z, changed, sse);
+                low_stats(o.w, c[u].w, changed, sse);
+            }
         }
     }
     // carrying bytes after the last whole vector
@@ -288,11 +331,21 @@ __global__ void __launch_bounds__(512) extractk_vec(KView a)
 #pragma unroll
         for (int t = 0; t < 16; ++t)
             X |= (uint64_t)((w[t >> 2] >> (8 * (t & 3))) & MASK) << (64 - K * (t + 1));
+        const uint64_t q0 = 2u * K * v; // first stream byte of the vector
+        uint8_t *op = a.out + (q0 - hb);
+        if ((K & 1) == 0 && q0 >= hb && q0 + 2 * K <= sbytes && (((uintptr_t)op & 3u) == 0)) {
+            // message bytes only, 4-byte aligned: K/2 word stores
 #pragma unroll
-        for (int i = 0; i < 2 * K; ++i) {
-            const uint64_t q = 2u * K * v + i; // stream byte
-            if (q >= hb && q < sbytes)
-                a.out[q - hb] = (uint8_t)(X >> (56 - 8 * i));
+            for (int i = 0; i < K / 2; ++i)
+                reinterpret_cast<uint32_t *>(op)[i] =
+                    __byte_perm((uint32_t)(X >> (32 - 32 * i)), 0u, 0x0123u);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2 * K; ++i) {
+                const uint64_t q = q0 + i; // stream byte
+                if (q >= hb && q < sbytes)
+                    a.out[q - hb] = (uint8_t)(X >> (56 - 8 * i));
+            }
         }
     }
 }
@@ -306,10 +359,21 @@ __global__ void __launch_bounds__(512) extractk_bytes(KView a)
     const uint64_t first = a.header ? 32u : 0u;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < len;
          s += (uint64_t)gridDim.x * blockDim.x) {
+        // walk the message byte's eight stream bits field by field: one
+        // division per byte, one load per carrying byte touched
+        const uint64_t b0 = first + 8u * s;
+        uint64_t x = b0 / a.k;
+        uint32_t r = (uint32_t)(b0 - x * a.k);
+        uint32_t cb = a.cover[carry_pos(a, x)];
         uint32_t v = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            v |= stream_bit(a, first + 8u * s + i) << (7 - i);
+        for (int i = 0; i < 8; ++i) {
+            v |= ((cb >> (a.k - 1u - r)) & 1u) << (7 - i);
+            if (++r == a.k && i < 7) {
+                r = 0;
+                cb = a.cover[carry_pos(a, ++x)];
+            }
+        }
         a.out[s] = (uint8_t)v;
     }
 }
@@ -351,7 +415,8 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
         default: kern = stats ? (const void *)embedk_vec<4, true> : (const void *)embedk_vec<4, false>; break;
         }
         const uint64_t nvec = a.n_carry >> 4;
-        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nvec ? nvec : 1, (uint64_t)T * 4);
+        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nvec ? nvec : 1,
+                                         (uint64_t)T); // one vector per thread
         return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
     }
     if (plane_only && !inplace) {
