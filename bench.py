@@ -35,16 +35,35 @@ UNIT = "cover GB/s"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic per launch of the dominant kernel (embed_vec<4,true>) from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on this exact
-# workload, valid only while the kernel sources hash to `src_sha`.
+# DRAM traffic per launch of the embed kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum) from one ncu capture on this exact workload, per
+# kernel family, valid only while the kernel sources hash to `src_sha`.
 # Writes still dirty in the L2 when the kernel exits are not in the count.
-NCU_TRAFFIC = {"embed": {"src_sha": "2e871efddda4b64f", "bytes": 226518528 + 143612416}}
+NCU_TRAFFIC = {"embed_vec": {"src_sha": "2e871efddda4b64f", "bytes": 226518528 + 143612416}}
+KERNEL_SOURCES = ("s1_device.cuh", "stream1.cu", "bulk.cu", "internal.cuh")
+MAX_RING = 192 * 1024
+
+
+def staged_stages(t) -> int:
+    """Stages of the shared-memory staged kernels for a single-cover shape
+    (0: the register kernels run), as the library derives them."""
+    if not t.tile_bytes:
+        return 0
+    tile = t.threads * 16 * t.vec_per_thread
+    st = min(8, t.tile_bytes // tile)
+    while st >= 2 and st * tile > MAX_RING:
+        st -= 1
+    return st if st >= 2 else 0
+
+
+def embed_kernel_name(t) -> tuple[str, str]:
+    fam = "embed_bulk" if staged_stages(t) else "embed_vec"
+    return fam, "%s<%d,true>" % (fam, t.vec_per_thread)
 
 
 def kernel_src_sha() -> str:
     h = hashlib.sha256()
-    for f in ("s1_device.cuh", "stream1.cu", "internal.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_0912_0947_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -166,12 +185,19 @@ def run_ours(args, rank, world, local_rank):
         S.stego_extract(stego, out, 0, fx, res_x, stream=stream)
 
     tuning = {}
-    if not args.no_tune:
-        embed()
-        for name, op, fn in (("embed", S.OP_EMBED, embed), ("extract", S.OP_EXTRACT, extract)):
+    fixed = {"embed": args.shape_embed, "extract": args.shape_extract}
+    embed()
+    for name, op, fn in (("embed", S.OP_EMBED, embed), ("extract", S.OP_EXTRACT, extract)):
+        if fixed[name]:
+            S.stego_set_tune(op, tuple(int(x) for x in fixed[name].split(",")))
+            tuning[name] = {"fixed": fixed[name]}
+        elif not args.no_tune:
             best, us, table = AT.autotune(op, fn, C, flush=flush, use_cache=False)
+            staged = [t for s_, t in table if s_[3]]
             tuning[name] = {"best": list(best), "us": round(us, 2), "candidates": len(table),
-                            "worst_us": round(max(t for _, t in table), 2)}
+                            "worst_us": round(max(t for _, t in table), 2),
+                            "best_register_us": round(min(t for s_, t in table if not s_[3]), 2),
+                            "best_staged_us": round(min(staged), 2) if staged else None}
 
     def step(ev=None):
         flush()
@@ -216,6 +242,15 @@ def run_ours(args, rank, world, local_rank):
     value = job_throughput(2.0 * C * args.steps, dev_ms, world)
 
     stats = S.read_result(res_e)
+    # ---- practical roofline: a same-size device copy, timed the same way ---
+    copy = None
+    if rank == 0:
+        t_copy = AT.time_call(lambda: stego.copy_(cover), flush, 20, stream=stream)
+        embed()  # restore the stego
+        copy_gbs = 2 * C / (t_copy * 1e-6) / 1e9
+        copy = {"what": "torch copy_ of the %d-byte cover into the stego buffer (2C bytes), "
+                        "L2 flushed, median of 20" % C,
+                "us": round(t_copy, 2), "gbs": round(copy_gbs, 1)}
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
     if (rank == 0 or world > 1) and args.e2e_steps > 0:
@@ -225,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
     legs = {}
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
                                                          "batched_video_paper2", "paper2",
-                                                         "streamk", "serving"}
+                                                         "streamk", "serving", "small"}
     if args.no_batched:
         want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk"}
     if args.no_serving:
@@ -242,6 +277,9 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and "streamk" in want:
         legs["streamk"] = run_streamk_leg(S, AT, torch, dev, synth)
         torch.cuda.empty_cache()
+    if rank == 0 and "small" in want:
+        legs["small_512x512x3"] = run_small_leg(S, AT, torch, dev, synth)
+        torch.cuda.empty_cache()
     if rank == 0 and "paper2" in want:
         legs["paper2"] = run_paper2_leg(S, AT, torch, dev, synth)
         torch.cuda.empty_cache()
@@ -252,7 +290,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- CPU oracle baseline ----------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(cover.cpu().numpy(), msg.cpu().numpy(), budget_s=args.cpu_seconds)
+        cover_h, msg_h = cover.cpu().numpy(), msg.cpu().numpy()
+        cpu = run_cpu_baseline(cover_h, msg_h, budget_s=args.cpu_seconds)
+        cpu["all_cores"] = run_cpu_all_cores(cover_h, msg_h, budget_s=args.cpu_seconds / 2)
 
     if rank != 0:
         return None
@@ -264,7 +304,10 @@ def run_ours(args, rank, world, local_rank):
     ext_us = statistics.mean(t_ext) * 1e3
     achieved = emb_bytes / (emb_us * 1e-6) / 1e9
     sha = kernel_src_sha()
-    traffic = NCU_TRAFFIC["embed"]["bytes"] if NCU_TRAFFIC["embed"]["src_sha"] == sha else None
+    t_emb_shape = S.stego_get_tune(S.OP_EMBED)
+    fam, kname = embed_kernel_name(t_emb_shape)
+    rec = NCU_TRAFFIC.get(fam)
+    traffic = rec["bytes"] if rec and rec["src_sha"] == sha else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -289,12 +332,17 @@ def run_ours(args, rank, world, local_rank):
         "extract": {"us": round(ext_us, 2), "cover_gbs": round(C / (ext_us * 1e-6) / 1e9, 1),
                     "algorithmic_bytes": ext_bytes,
                     "hbm_frac": round(ext_bytes / (ext_us * 1e-6) / 1e9 / peak, 4)},
-        "roofline": {"bound": "hbm", "kernel": "embed_vec<4,true> (stego_embed, fused stats)",
+        "roofline": {"bound": "hbm", "kernel": kname + " (stego_embed, fused stats)",
+                     "stages": staged_stages(t_emb_shape),
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic,
                      "note": "achieved = (2C + T/8) bytes / mean event time of the stego_embed "
                              "call (its 16-byte result memset included)"},
+        "copy_roofline": dict(copy, embed_frac_of_copy=round(achieved / copy["gbs"], 4),
+                              extract_frac_of_copy=round(
+                                  ext_bytes / (ext_us * 1e-6) / 1e9 / copy["gbs"], 4))
+        if copy else None,
         "psnr_db": round(10.0 * __import__("math").log10(255.0 ** 2 * C / stats["sse"]), 4)
         if stats["sse"] else None,
         "gpu_launches": 2 * args.steps,
@@ -409,17 +457,66 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
     same = all(torch.equal(sb[i], s1[i]) and torch.equal(ob[i], o1[i]) for i in range(n))
     assert same, "batched and per-image outputs differ"
     assert all(torch.equal(ob[i], mv[i]) for i in range(n)), "batched round trip differs"
+    extra = {}
+    if kind != "uneven":
+        # in place (stego == cover): re-embedding the same message is idempotent
+        inpl = covers.clone()
+        iv = [inpl[o:o + c] for o, c in zip(off, sizes)]
+        d_inp = S.descs_to_device(S.pack_descs(
+            [dict(cover=iv[i], stego=iv[i], msg=mv[i], cover_bytes=sizes[i],
+                  msg_bytes=mlens[i], flags=hdr, **geo) for i in range(n)]), dev)
+        t_bi = AT.time_call(lambda: S.stego_embed_batched(d_inp, n, res_b, S.FUSE_STATS, ws,
+                                                          stream=stream), flush, 7)
+        torch.cuda.synchronize()
+        assert all(torch.equal(iv[i], sb[i]) for i in range(n)), "in-place batched differs"
+        extra["embed_in_place_batched_us"] = round(t_bi, 1)
+        del inpl, iv, d_inp
+    else:
+        # the same covers as separate allocations (one tensor per cover,
+        # message and output) instead of slots of one arena
+        sc = [x.clone() for x in cv]
+        ss = [torch.empty_like(x) for x in sc]
+        sm = [x.clone() for x in mv]
+        so = [torch.empty_like(x) for x in sm]
+        d_se = S.descs_to_device(S.pack_descs(
+            [dict(cover=sc[i], stego=ss[i], msg=sm[i], cover_bytes=sizes[i],
+                  msg_bytes=mlens[i], flags=hdr) for i in range(n)]), dev)
+        d_sx = S.descs_to_device(S.pack_descs(
+            [dict(cover=ss[i], msg=so[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+                  flags=hdr) for i in range(n)]), dev)
+        t_se = AT.time_call(lambda: S.stego_embed_batched(d_se, n, res_b, S.FUSE_STATS, ws,
+                                                          stream=stream), flush, 7)
+        t_sx = AT.time_call(lambda: S.stego_extract_batched(d_sx, n, res_b, 0, ws,
+                                                            stream=stream), flush, 7)
+        torch.cuda.synchronize()
+        assert all(torch.equal(ss[i], sb[i]) and torch.equal(so[i], mv[i]) for i in range(n)), \
+            "separate-tensor batched differs"
+        extra["separate_tensors"] = {"embed_batched_us": round(t_se, 1),
+                                     "extract_batched_us": round(t_sx, 1)}
+        del sc, ss, sm, so
     total = sum(sizes)
     if paper:  # out of place 2C + N; extraction touches every sector of its rows
         emb_bytes = sum(2 * c + m for c, m in zip(sizes, mlens))
         rows = [-(-m // (v.width // 4)) for m in mlens]
         ext_bytes = sum(r * v.width * 3 + m for r, m in zip(rows, mlens))
+        # in place: the carrying plane bytes' sectors of the carrying rows
+        inp_bytes = sum(2 * r * v.width * 3 + m for r, m in zip(rows, mlens))
     else:
         T = [8 * (m + 4) for m in mlens]
         emb_bytes = sum(2 * c + t // 8 for c, t in zip(sizes, T))
         ext_bytes = sum(t + t // 8 for t in T)
+        inp_bytes = sum(2 * t + t // 8 for t in T)
     peak, _ = hbm_peak()
     gbs = lambda b, us: round(b / (us * 1e-6) / 1e9, 1)
+    if "embed_in_place_batched_us" in extra:
+        t_bi = extra["embed_in_place_batched_us"]
+        extra["embed_in_place"] = {"algorithmic_bytes": inp_bytes,
+                                   "cover_gbs": gbs(total, t_bi),
+                                   "hbm_frac": round(inp_bytes / (t_bi * 1e-6) / 1e9 / peak, 4)}
+    if "separate_tensors" in extra:
+        st_ = extra["separate_tensors"]
+        st_["embed_cover_gbs"] = gbs(total, st_["embed_batched_us"])
+        st_["extract_cover_gbs"] = gbs(total, st_["extract_batched_us"])
     return {
         "workload": ("4096 uneven covers (log-uniform sides 64..4096, 1 or 3 channels, "
                      "5-100% fill)" if kind == "uneven" else
@@ -439,6 +536,7 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
                              "extract": round(ext_bytes / (t_bx * 1e-6) / 1e9 / peak, 4)},
         "launch": tune_sel,
         "outputs_identical": same,
+        **extra,
     }
 
 
@@ -618,6 +716,58 @@ def run_streamk_leg(S, AT, torch, dev, synth):
     return out
 
 
+def run_small_leg(S, AT, torch, dev, synth, reps=25, burst=1000):
+    """The 512x512x3 cover (786,432 bytes) with a 32,768-byte message behind
+    the header: the whole working set fits the L2, so the time is launch and
+    latency bound.  Cold = L2 flushed before each call, warm = after an
+    untimed run of the same call (both with the call queued before its start
+    event); back to back = `burst` calls between two events (device time per
+    call, launch gaps included); enqueue = host time per API call."""
+    w = synth.single_512()
+    C, m = w.cover_bytes, w.msg_bytes
+    cover, msg = w.cover(dev), w.message(dev)
+    stego = torch.empty_like(cover)
+    out = torch.empty(m, dtype=torch.uint8, device=dev)
+    res_e, res_x = S.new_result(dev), S.new_result(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = AT.Flusher(dev)
+
+    def emb():
+        S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res_e, stream=stream)
+
+    def ext():
+        S.stego_extract(stego, out, 0, S.HEADER_BE32, res_x, stream=stream)
+
+    r = {"workload": "512x512x3 uint8 cover, 32768-byte message + 32-bit header "
+                     "(T = 262176 carrying bytes)"}
+    for name, fn in (("embed", emb), ("extract", ext)):
+        fn()
+        cold = AT.time_call(fn, flush, reps, stream=stream)
+
+        def warm_up(fn=fn):  # the same call untimed (its data now in L2), then a spin
+            fn()
+            torch.cuda._sleep(AT.SPIN_CYCLES)
+
+        warm = AT.time_call(fn, warm_up, reps, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(burst):
+            fn()
+        e1.record(stream)
+        t_host = time.perf_counter() - t0
+        torch.cuda.synchronize(dev)
+        b2b = e0.elapsed_time(e1) * 1e3 / burst
+        r[name] = {"cold_us": round(cold, 2), "warm_us": round(warm, 2),
+                   "back_to_back_us": round(b2b, 2),
+                   "enqueue_us": round(t_host * 1e6 / burst, 2),
+                   "cover_gbs_cold": round(C / (cold * 1e-6) / 1e9, 1),
+                   "cover_gbs_back_to_back": round(C / (b2b * 1e-6) / 1e9, 1)}
+    assert torch.equal(out, msg)
+    return r
+
+
 def tune_dict(t):
     return {"threads": t.threads, "vec_per_thread": t.vec_per_thread,
             "ctas_per_sm": t.ctas_per_sm, "tile_bytes": t.tile_bytes}
@@ -732,8 +882,33 @@ def run_cpu_baseline(cover, msg, budget_s=12.0):
         reps += 1
     return {"value": round(2.0 * cover.size * reps / elapsed / 1e9, 4), "unit": UNIT,
             "cores": 1, "kind": "oracle",
-            "sample": "%d embed+extract round trips of the whole 201,326,592-byte cover "
-                      "(single-threaded C oracle, %.1f s)" % (reps, elapsed)}
+            "sample": "%d embed+extract round trips of the whole %d-byte cover "
+                      "(single-threaded C oracle, %.1f s)" % (reps, cover.size, elapsed)}
+
+
+def run_cpu_all_cores(cover, msg, budget_s=6.0):
+    """The same oracle on every host core: the cover is cut into one
+    independent cover per core (16-byte multiples), each carrying its own
+    full-capacity message, and the round trips run in parallel threads (the
+    oracle's C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    O = oracle.load()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    part = cover.size // cores // 16 * 16
+    jobs = [(cover[i * part:(i + 1) * part], msg[:part // 8 - 4]) for i in range(cores)]
+    reps, elapsed = 0, 0.0
+    with ThreadPoolExecutor(cores) as ex:
+        while elapsed < budget_s and reps < 50:
+            t0 = time.perf_counter()
+            list(ex.map(lambda j: oracle_round_trip(O, j[0], j[1]), jobs))
+            elapsed += time.perf_counter() - t0
+            reps += 1
+    return {"value": round(2.0 * part * cores * reps / elapsed / 1e9, 4), "unit": UNIT,
+            "cores": cores, "kind": "oracle",
+            "sample": "%d rounds of %d parallel embed+extract round trips, one independent "
+                      "%d-byte cover per core cut from the same cover (%.1f s)"
+                      % (reps, cores, part, elapsed)}
 
 
 def run_reference(args, rank, world):
@@ -791,6 +966,10 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--shape-embed", default="",
+                    help="fixed launch shape threads,vec,ctas_per_sm,tile_bytes for the embed "
+                         "(tile_bytes > 0: shared-memory staged kernel with that ring)")
+    ap.add_argument("--shape-extract", default="", help="same for the extract")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--uneven-count", type=int, default=0,
@@ -798,7 +977,8 @@ def main():
     ap.add_argument("--video-frames", type=int, default=0,
                     help="frames in the video batched leg (default 600)")
     ap.add_argument("--legs", default="",
-                    help="comma list of extra legs: batched_uneven,batched_video,paper2,serving "
+                    help="comma list of extra legs: batched_uneven,batched_video,"
+                         "batched_video_paper2,paper2,streamk,serving,small, or none "
                          "(default all)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -69,7 +69,7 @@ enum stego_status {
     STEGO_E_MSG_TOO_SMALL = -4, /* output message buffer smaller than length  */
     STEGO_E_CUDA = -5,          /* a CUDA runtime call failed                 */
     STEGO_E_NOMEM = -6,         /* caller-supplied workspace too small        */
-    STEGO_E_TIMEOUT = -7        /* reserved for bounded device-side waits     */
+    STEGO_E_TIMEOUT = -7        /* a bounded device-side wait ran out         */
 };
 
 /* ------------------------------------------------------------------ */
@@ -149,8 +149,17 @@ typedef struct stego_desc {
  *   vec_per_thread  16-byte vectors each thread keeps in flight per loop
  *                   iteration (1, 2, 4 or 8)
  *   ctas_per_sm     resident CTAs per SM of the persistent grid
- *   tile_bytes      batched calls: cover bytes per work tile (a multiple of
- *                   4096, at least 4096) */
+ *   tile_bytes      a multiple of 4096.  Batched calls: cover bytes per work
+ *                   tile (at least 4096).  Single-cover one-bit STREAM1
+ *                   embed and extract on 16-byte aligned buffers: 0 selects
+ *                   the register-streaming kernels; otherwise the kernels
+ *                   staged through shared memory by bulk asynchronous
+ *                   copies, with a ring of tile_bytes bytes per CTA cut into
+ *                   stages of threads * 16 * vec_per_thread bytes (2 to 8
+ *                   stages, at most 192 KiB; a ring smaller than two stages
+ *                   selects the register kernels).  For STEGO_OP_EMBED and
+ *                   STEGO_OP_EXTRACT, stego_set_tune installs tile_bytes as
+ *                   given, 0 included. */
 typedef struct stego_tune {
     uint32_t threads;
     uint32_t vec_per_thread;

@@ -1,7 +1,9 @@
 """Launch-shape autotuner.
 
 Times candidate launch shapes (threads per CTA, 16-byte vectors in flight
-per thread, resident CTAs per SM, and for batched calls the tile size) of
+per thread, resident CTAs per SM, for batched calls the tile size, and for
+the single-cover embed/extract the choice between the register kernels and
+the shared-memory staged kernels with their ring size) of
 one operation on the caller's own buffers with CUDA events, flushing the L2
 between repetitions, and installs the fastest with ``stego_set_tune`` so
 every later call of that operation uses it.  Choices are cached per device
@@ -22,6 +24,12 @@ from . import Tune, stego_get_tune, stego_set_tune
 L2_FLUSH_BYTES = 256 << 20
 
 SINGLE_CANDIDATES = [(t, v, c) for t in (128, 256, 512) for v in (2, 4, 8) for c in (0, 2, 4, 8)]
+# shared-memory staged kernels of the one-bit embed/extract: tile_bytes is
+# the ring per CTA, cut into stages of threads * 16 * v bytes
+STAGED_CANDIDATES = [(t, v, 0, ring)
+                     for t, v in ((128, 4), (128, 8), (256, 2), (256, 4), (256, 8), (512, 2),
+                                  (512, 4))
+                     for ring in (65536, 131072) if ring >= 2 * t * 16 * v]
 BATCHED_CANDIDATES = [(t, v, 0, tile) for t in (256, 512) for v in (2, 4, 8)
                       for tile in (16384, 65536, 262144, 1 << 20)]
 
@@ -125,7 +133,12 @@ def autotune(op: int, fn, size_bytes: int, candidates=None, flush=None, reps: in
         if hit is not None:
             return tuple(hit["shape"]), hit["us"], []
     if candidates is None:
-        candidates = BATCHED_CANDIDATES if op >= 3 else SINGLE_CANDIDATES
+        if op >= 3:
+            candidates = BATCHED_CANDIDATES
+        elif op in (0, 1):  # embed, extract
+            candidates = SINGLE_CANDIDATES + STAGED_CANDIDATES
+        else:
+            candidates = SINGLE_CANDIDATES
     flush = flush or Flusher(device or torch.cuda.current_device())
     old = stego_get_tune(op)
     table = []

@@ -28,6 +28,7 @@ struct OccEntry {
     int threads;
     int device;
     int blocks;
+    size_t smem;
 };
 constexpr int kOccSlots = 128;
 OccEntry g_occ[kOccSlots];
@@ -40,7 +41,8 @@ int occupancy(const void *kernel, int threads, size_t smem)
     {
         std::lock_guard<std::mutex> lk(g_mu);
         for (int i = 0; i < g_occ_n; ++i)
-            if (g_occ[i].kernel == kernel && g_occ[i].threads == threads && g_occ[i].device == dev)
+            if (g_occ[i].kernel == kernel && g_occ[i].threads == threads &&
+                g_occ[i].device == dev && g_occ[i].smem == smem)
                 return g_occ[i].blocks;
     }
     int blocks = 0;
@@ -50,7 +52,7 @@ int occupancy(const void *kernel, int threads, size_t smem)
         blocks = 1;
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_occ_n < kOccSlots)
-        g_occ[g_occ_n++] = OccEntry{kernel, threads, dev, blocks};
+        g_occ[g_occ_n++] = OccEntry{kernel, threads, dev, blocks, smem};
     return blocks;
 }
 
@@ -433,7 +435,8 @@ int stego_set_tune(int op, const stego_tune *t)
     if (t->vec_per_thread)
         s.vec = (int)t->vec_per_thread;
     s.ctas_per_sm = (int)t->ctas_per_sm; // 0 restores "occupancy maximum"
-    if (t->tile_bytes)
+    // single-cover calls: 0 selects the register kernels, so it is installed too
+    if (t->tile_bytes || op == STEGO_OP_EMBED || op == STEGO_OP_EXTRACT)
         s.tile_bytes = t->tile_bytes;
     return STEGO_OK;
 }

@@ -17,7 +17,9 @@ struct Shape {
     int threads;         // threads per CTA
     int vec;             // 16-byte vectors per thread per loop iteration
     int ctas_per_sm;     // 0 = as many as occupancy allows
-    uint32_t tile_bytes; // batched: cover bytes per tile
+    uint32_t tile_bytes; // batched: cover bytes per tile; single-cover STREAM1:
+                         // 0 = register kernels, else ring bytes per CTA of
+                         // the shared-memory staged kernels
 };
 
 // The shape installed for `op`, with the fields of `override_` (if non-null
@@ -81,6 +83,19 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
 cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_only,
                        const stego_geom *g, uint8_t *msg, uint64_t cap, uint64_t raw_len,
                        bool header, stego_result *res, const Shape &sh, cudaStream_t s);
+
+// STREAM1 kernels staged through shared memory with bulk asynchronous
+// copies (bulk.cu); same arguments and results as s1_embed / s1_extract.
+// Usable with 16-byte aligned buffers when bulk_stages(sh) >= 2: a shape
+// with tile_bytes = ring bytes per CTA, tiles of threads * 16 * vec bytes.
+uint32_t bulk_stages(const Shape &sh);
+cudaError_t s1_embed_bulk(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes,
+                          uint64_t t_bytes, const uint8_t *msg, uint64_t slen, bool header,
+                          uint32_t nbits, bool stats, stego_result *res, uint64_t res_msg_bytes,
+                          const Shape &sh, cudaStream_t s);
+cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
+                            uint64_t raw_len, bool header, stego_result *res, const Shape &sh,
+                            cudaStream_t s);
 
 // Changed-byte count and SSE of two arrays into out2[0..1] (zeroed by the
 // caller).

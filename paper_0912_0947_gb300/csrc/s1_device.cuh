@@ -85,6 +85,31 @@ __device__ __forceinline__ uint32_t spread_lo(uint32_t rep)
 // is also the word's squared error.
 __device__ __forceinline__ uint32_t lsb_changes(uint32_t o, uint32_t c) { return __popc(o ^ c); }
 
+// Cover vector v (bytes 16v..16v+15) with its stream bytes p = S[2v] |
+// S[2v+1] << 8 -> stego vector; n += changed bytes when STATS.
+template <bool STATS>
+__device__ __forceinline__ uint4 embed_vec16(const EmbedView &a, uint64_t v, const uint4 &c,
+                                             uint32_t p, uint32_t &n)
+{
+    uint4 o = c;
+    const uint64_t k0 = v << 4;
+    if (k0 < a.t_bytes) {
+        const uint32_t r0 = __byte_perm(p, 0u, 0x0000u);
+        o.x = (c.x & 0xFEFEFEFEu) | spread_hi(r0);
+        o.y = (c.y & 0xFEFEFEFEu) | spread_lo(r0);
+        if (STATS)
+            n += lsb_changes(o.x, c.x) + lsb_changes(o.y, c.y);
+        if (k0 + 8 < a.t_bytes) { // T is a multiple of 8
+            const uint32_t r1 = __byte_perm(p, 0u, 0x1111u);
+            o.z = (c.z & 0xFEFEFEFEu) | spread_hi(r1);
+            o.w = (c.w & 0xFEFEFEFEu) | spread_lo(r1);
+            if (STATS)
+                n += lsb_changes(o.z, c.z) + lsb_changes(o.w, c.w);
+        }
+    }
+    return o;
+}
+
 // 16-byte vectors v = v_first + i*step (+ u*blockDim.x for u < V), v < v_end,
 // of a job whose cover and stego are 16-byte aligned.  Each warp's 128-bit
 // load and store instructions cover 512 contiguous bytes.  With STATS the
@@ -120,23 +145,7 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
             const uint64_t v = v0 + (uint64_t)u * blockDim.x;
             if (v >= v_end)
                 continue;
-            uint4 o = c[u];
-            const uint64_t k0 = v << 4;
-            if (k0 < a.t_bytes) {
-                const uint32_t r0 = __byte_perm(p[u], 0u, 0x0000u);
-                o.x = (c[u].x & 0xFEFEFEFEu) | spread_hi(r0);
-                o.y = (c[u].y & 0xFEFEFEFEu) | spread_lo(r0);
-                if (STATS)
-                    n += lsb_changes(o.x, c[u].x) + lsb_changes(o.y, c[u].y);
-                if (k0 + 8 < a.t_bytes) { // T is a multiple of 8
-                    const uint32_t r1 = __byte_perm(p[u], 0u, 0x1111u);
-                    o.z = (c[u].z & 0xFEFEFEFEu) | spread_hi(r1);
-                    o.w = (c[u].w & 0xFEFEFEFEu) | spread_lo(r1);
-                    if (STATS)
-                        n += lsb_changes(o.z, c[u].z) + lsb_changes(o.w, c[u].w);
-                }
-            }
-            __stcs(dst + v, o);
+            __stcs(dst + v, embed_vec16<STATS>(a, v, c[u], p[u], n));
         }
         if (STATS) {
             changed += n;
@@ -284,6 +293,59 @@ __device__ __forceinline__ uint32_t warp_read_header(const uint8_t *st, uint64_t
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t byte = (lane < C) ? (uint32_t)st[lane] : 0u;
     return __brev(__ballot_sync(0xFFFFFFFFu, byte & 1u));
+}
+
+struct ExtractArgs {
+    const uint8_t *st;
+    uint64_t C;
+    uint8_t *msg;
+    uint64_t cap;
+    uint64_t raw_len;
+    uint32_t header;
+    uint32_t msg_even;
+    stego_result *res;
+};
+
+// Length and status of the call: from the header (read by warp 0 of every
+// CTA with one ballot) or the caller's length.  Block 0 publishes them.
+__device__ __forceinline__ int extract_prologue(const ExtractArgs &a, ExtractView &x)
+{
+    __shared__ int s_status;
+    __shared__ unsigned long long s_len;
+    x.st = a.st;
+    x.msg = a.msg;
+    x.msg_even = a.msg_even;
+    x.pad = 0;
+    if (a.header) {
+        if (threadIdx.x < 32) {
+            const uint32_t nbits = s1::warp_read_header(a.st, a.C);
+            if (threadIdx.x == 0) {
+                const int st = s1::header_status(a.C, a.cap, nbits);
+                s_status = st;
+                s_len = st == STEGO_OK ? (nbits >> 3) : 0u;
+            }
+        }
+        __syncthreads();
+        x.len = s_len;
+        x.base = 32;
+    } else {
+        if (threadIdx.x == 0) {
+            s_status = STEGO_OK;
+            s_len = a.raw_len;
+        }
+        __syncthreads();
+        x.len = a.raw_len;
+        x.base = 0;
+    }
+    const int status = s_status;
+    if (a.res && blockIdx.x == 0 && threadIdx.x == 0) {
+        a.res->changed = 0;
+        a.res->sse = 0;
+        a.res->msg_bytes = x.len;
+        a.res->status = status;
+        a.res->reserved = 0;
+    }
+    return status;
 }
 
 } // namespace s1

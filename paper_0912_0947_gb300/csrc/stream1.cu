@@ -65,58 +65,8 @@ __global__ void __launch_bounds__(512) embed_bytes(EmbedArgs e)
         block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&e.res->changed));
 }
 
-struct ExtractArgs {
-    const uint8_t *st;
-    uint64_t C;
-    uint8_t *msg;
-    uint64_t cap;
-    uint64_t raw_len;
-    uint32_t header;
-    uint32_t msg_even;
-    stego_result *res;
-};
-
-// Length and status of the call: from the header (read by warp 0 of every
-// CTA with one ballot) or the caller's length.  Block 0 publishes them.
-__device__ __forceinline__ int extract_prologue(const ExtractArgs &a, ExtractView &x)
-{
-    __shared__ int s_status;
-    __shared__ unsigned long long s_len;
-    x.st = a.st;
-    x.msg = a.msg;
-    x.msg_even = a.msg_even;
-    x.pad = 0;
-    if (a.header) {
-        if (threadIdx.x < 32) {
-            const uint32_t nbits = s1::warp_read_header(a.st, a.C);
-            if (threadIdx.x == 0) {
-                const int st = s1::header_status(a.C, a.cap, nbits);
-                s_status = st;
-                s_len = st == STEGO_OK ? (nbits >> 3) : 0u;
-            }
-        }
-        __syncthreads();
-        x.len = s_len;
-        x.base = 32;
-    } else {
-        if (threadIdx.x == 0) {
-            s_status = STEGO_OK;
-            s_len = a.raw_len;
-        }
-        __syncthreads();
-        x.len = a.raw_len;
-        x.base = 0;
-    }
-    const int status = s_status;
-    if (a.res && blockIdx.x == 0 && threadIdx.x == 0) {
-        a.res->changed = 0;
-        a.res->sse = 0;
-        a.res->msg_bytes = x.len;
-        a.res->status = status;
-        a.res->reserved = 0;
-    }
-    return status;
-}
+using s1::ExtractArgs;
+using s1::extract_prologue;
 
 // Vector path: stego 16-byte aligned.
 template <int V>
@@ -167,6 +117,9 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
     e.res_msg_bytes = res_msg_bytes;
     const int T = sh.threads;
     void *args[] = {&e};
+    if (aligned16(cover) && aligned16(stego) && bulk_stages(sh))
+        return s1_embed_bulk(cover, stego, n_bytes, t_bytes, msg, slen, header, nbits, stats,
+                             res, res_msg_bytes, sh, s);
     if (aligned16(cover) && aligned16(stego)) {
         const int vec = clamp_vec(sh.vec);
         const void *k = nullptr;
@@ -208,6 +161,8 @@ cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap
     }
     const int T = sh.threads;
     void *args[] = {&a};
+    if (aligned16(st) && bulk_stages(sh))
+        return s1_extract_bulk(st, C, msg, cap, raw_len, header, res, sh, s);
     if (aligned16(st)) {
         const int vec = clamp_vec(sh.vec);
         const void *k;

@@ -75,6 +75,15 @@ def test_tune_validation(built):
     S.stego_set_tune(S.OP_EMBED, (128, 2, 3, 0))
     t = S.stego_get_tune(S.OP_EMBED)
     assert (t.threads, t.vec_per_thread, t.ctas_per_sm) == (128, 2, 3)
+    # single-cover calls install tile_bytes as given (0 = register kernels),
+    # batched calls keep their tile when given 0
+    S.stego_set_tune(S.OP_EMBED, (256, 4, 0, 65536))
+    assert S.stego_get_tune(S.OP_EMBED).tile_bytes == 65536
+    S.stego_set_tune(S.OP_EMBED, (256, 4, 0, 0))
+    assert S.stego_get_tune(S.OP_EMBED).tile_bytes == 0
+    oldb = S.stego_get_tune(S.OP_EXTRACT_BATCHED)
+    S.stego_set_tune(S.OP_EXTRACT_BATCHED, (256, 4, 0, 0))
+    assert S.stego_get_tune(S.OP_EXTRACT_BATCHED).tile_bytes == oldb.tile_bytes
     S.stego_set_tune(S.OP_EMBED, old)
 
 

@@ -78,7 +78,7 @@ def test_autotune_picks_restores_and_caches(tmp_path, monkeypatch):
 
     def fake_time(fn, flush, reps=15, stream=None):
         t = S.stego_get_tune(S.OP_EXTRACT)
-        seen.append((t.threads, t.vec_per_thread, t.ctas_per_sm))
+        seen.append((t.threads, t.vec_per_thread, t.ctas_per_sm, t.tile_bytes))
         # fastest at 256 threads, 8 vectors, 2 CTAs per SM
         return abs(t.threads - 256) / 64 + abs(t.vec_per_thread - 8) + abs(t.ctas_per_sm - 2) + 10.0
 
@@ -87,10 +87,12 @@ def test_autotune_picks_restores_and_caches(tmp_path, monkeypatch):
     try:
         best, us, table = AT.autotune(S.OP_EXTRACT, lambda: None, 1 << 27, flush=lambda: None,
                                       use_cache=False)
-        assert best[:3] == (256, 8, 2) and us == 10.0 and len(table) == len(AT.SINGLE_CANDIDATES)
+        n_cand = len(AT.SINGLE_CANDIDATES) + len(AT.STAGED_CANDIDATES)
+        assert best == (256, 8, 2, 0) and us == 10.0 and len(table) == n_cand
         t = S.stego_get_tune(S.OP_EXTRACT)
-        assert (t.threads, t.vec_per_thread, t.ctas_per_sm) == (256, 8, 2)  # installed
-        assert len(set(seen)) == len(AT.SINGLE_CANDIDATES)
+        assert (t.threads, t.vec_per_thread, t.ctas_per_sm, t.tile_bytes) == (256, 8, 2, 0)
+        assert len(set(seen)) == n_cand  # every candidate installed, staged ones included
+        assert {x[3] for x in seen} == {0, 65536, 131072}
         S.stego_set_tune(S.OP_EXTRACT, (128, 2, 0, 0))
         hit = AT.load_cached(S.OP_EXTRACT, 1 << 27)  # same size class: cached and installed
         assert hit["shape"][:3] == [256, 8, 2]
