@@ -11,20 +11,22 @@
 // all bytes is handled by stream1.cu.
 //
 // Kernels:
-//   embedk_vec<K,STATS>  all bytes, 16-byte aligned cover and stego: a
-//       16-byte vector carries 16K stream bits = stream bytes [2Kv, 2Kv+2K),
-//       assembled big-endian into one 64-bit word and cut into 16 K-bit
-//       fields; traffic 2C + 8|S|/8 out of place.
+//   embedk_units<K,CH,PLANE,STATS>  16-byte aligned cover and stego, all
+//       bytes (CH = 1) or one plane of 3 or 4 channels: a unit of 16
+//       carrying bytes (CH vectors of the cover) carries 16K stream bits =
+//       stream bytes [2Ku, 2Ku+2K), assembled big-endian into one 64-bit
+//       word and cut into 16 K-bit fields; out of place the whole cover
+//       moves once, 2C + |S| bytes.
 //   embedk_bytes<STATS>  any alignment, any k, either carrying order: one
 //       thread per carrying byte (out of place with one plane, after a copy
 //       of the cover).
-//   extractk_vec<K>  all bytes, 16-byte aligned stego.
+//   extractk_units<K,CH,PLANE>  16-byte aligned stego, same layouts.
 //   extractk_bytes  any alignment, any k, either carrying order.
 // The header's 32 bits are read by warp 0 of each CTA: lane l loads stream
 // bit l from its carrying byte and one ballot gathers them.
 #include <cstring>
 
-#include "internal.cuh"
+#include "s1_device.cuh"
 
 namespace stego {
 namespace {
@@ -142,83 +144,238 @@ __device__ __forceinline__ uint64_t stream_window(const KView &a, uint64_t v)
     return X;
 }
 
-// Grid-stride over 16-byte vectors (V per thread per iteration, cover and
-// stream loads issued before any arithmetic).
-template <int K, bool STATS>
-__global__ void __launch_bounds__(512) embedk_vec(KView a)
+// A unit is 16 consecutive carrying bytes: 16 consecutive cover bytes (all
+// bytes, CH = 1) or the plane bytes of 16 consecutive pixels (CH = 3 or 4
+// channels, plane PLANE), i.e. CH 16-byte vectors of the cover.  Pixel t's
+// plane byte is unit byte t*CH + PLANE, a compile-time position, so the 16
+// carrying bytes are gathered into one 16-byte value, transformed as one
+// vector of the all-bytes layout, and the change is XORed back.
+template <int CH>
+__device__ __forceinline__ void load_unit(const uint8_t *base, uint64_t u, uint32_t (&w)[4 * CH])
 {
-    constexpr int V = 1; // more in flight measured slower (registers)
+    const uint4 *p = reinterpret_cast<const uint4 *>(base) + u * CH;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+        const uint4 c = __ldcs(p + j);
+        w[4 * j] = c.x;
+        w[4 * j + 1] = c.y;
+        w[4 * j + 2] = c.z;
+        w[4 * j + 3] = c.w;
+    }
+}
+
+template <int CH>
+__device__ __forceinline__ void store_unit(uint8_t *base, uint64_t u, const uint32_t (&w)[4 * CH])
+{
+    uint4 *p = reinterpret_cast<uint4 *>(base) + u * CH;
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+        __stcs(p + j, make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]));
+}
+
+// The unit's 16 carrying bytes, byte t of word t/4 = carrying byte t.
+template <int CH, int PLANE>
+__device__ __forceinline__ void gather_unit(const uint32_t (&w)[4 * CH], uint32_t (&g)[4])
+{
+    if constexpr (CH == 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            g[i] = w[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            g[i] = 0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int pos = (4 * i + l) * CH + PLANE; // unit byte of carrying byte 4i+l
+                g[i] |= ((w[pos >> 2] >> (8 * (pos & 3))) & 0xFFu) << (8 * l);
+            }
+        }
+    }
+}
+
+// XOR of carrying-byte differences d (gathered order) into the unit's words.
+template <int CH, int PLANE>
+__device__ __forceinline__ void scatter_xor(uint32_t (&w)[4 * CH], const uint32_t (&d)[4])
+{
+    if constexpr (CH == 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            w[i] ^= d[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int pos = (4 * i + l) * CH + PLANE;
+                w[pos >> 2] ^= ((d[i] >> (8 * l)) & 0xFFu) << (8 * (pos & 3));
+            }
+        }
+    }
+}
+
+// Word i (carrying bytes 4i..4i+3, field in each byte's low K bits) of a
+// unit whose stream window is X (stream bytes big-endian, the first in bits
+// 56..63).  K = 1, 2, 4 fill the four byte lanes from replicated stream
+// bytes with fixed per-lane shifts; K = 3 (fields across byte boundaries)
+// cuts the 64-bit window field by field.
+template <int K>
+__device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
+{
+    const uint32_t hi = (uint32_t)(X >> 32), lo = (uint32_t)X;
+    if constexpr (K == 1) {
+        // stream byte i/2; even words take its bits 7..4, odd words 3..0
+        const uint32_t r = __byte_perm(hi, 0u, i < 2 ? 0x3333u : 0x2222u);
+        return (i & 1) ? s1::spread_lo(r) : s1::spread_hi(r);
+    } else if constexpr (K == 2) {
+        // stream byte i; lane l takes its bits 7-2l and 6-2l
+        const uint32_t sel = 0x3333u - 0x1111u * (uint32_t)i;
+        const uint32_t r = __byte_perm(hi, 0u, sel);
+        return ((r >> 6) & 0x03u) | ((r >> 4) & 0x0300u) | ((r >> 2) & 0x030000u) |
+               (r & 0x03000000u);
+    } else if constexpr (K == 4) {
+        // stream bytes 2i, 2i+1; lanes take high nibble, low nibble, high, low
+        const uint32_t r = __byte_perm(i < 2 ? hi : lo, 0u, (i & 1) ? 0x0011u : 0x2233u);
+        return ((r >> 4) & 0x000F000Fu) | (r & 0x0F000F00u);
+    } else {
+        constexpr uint32_t MASK = (1u << K) - 1u;
+        uint32_t f = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            f |= (uint32_t)((X >> (64 - K * (4 * i + l + 1))) & MASK) << (8 * l);
+        return f;
+    }
+}
+
+// The inverse: a unit's stream window from its 16 carrying bytes g (words
+// of four), fields in the low K bits.  K = 1 and 2 gather the four lanes of
+// a word with one multiply (the partial products of the wanted bits land in
+// disjoint bit ranges of the top byte, all others below it or past bit 31);
+// K = 4 joins nibble pairs.
+template <int K>
+__device__ __forceinline__ uint64_t unit_window(const uint32_t (&g)[4])
+{
+    if constexpr (K == 1) {
+        const uint32_t b0 = (s1::gather4(g[0]) << 4) | s1::gather4(g[1]);
+        const uint32_t b1 = (s1::gather4(g[2]) << 4) | s1::gather4(g[3]);
+        return (uint64_t)((b0 << 24) | (b1 << 16)) << 32;
+    } else if constexpr (K == 2) {
+        uint32_t hi = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) // lane l -> bits 30-2l, 31-2l of the product
+            hi |= (((g[i] & 0x03030303u) * 0x40100401u) >> 24) << (24 - 8 * i);
+        return (uint64_t)hi << 32;
+    } else if constexpr (K == 4) {
+        uint32_t b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t m = g[i] & 0x0F0F0F0Fu;
+            b[i] = ((m << 4) | (m >> 8)) & 0x00FF00FFu; // bytes 2i (lane 0), 2i+1 (lane 2)
+        }
+        const uint32_t hi = __byte_perm(b[0], b[1], 0x0246u); // b0.l0 b0.l2 b1.l0 b1.l2, first on top
+        const uint32_t lo = __byte_perm(b[2], b[3], 0x0246u);
+        return ((uint64_t)hi << 32) | lo;
+    } else {
+        constexpr uint32_t MASK = (1u << K) - 1u;
+        uint64_t X = 0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            X |= (uint64_t)((g[t >> 2] >> (8 * (t & 3))) & MASK) << (64 - K * (t + 1));
+        return X;
+    }
+}
+
+// Units each thread keeps in flight per loop iteration.  A plane unit is
+// already CH vectors; all-bytes units are single vectors, of which the
+// extract batches four (measured on the 201 MB cover, k = 2: 43.0 us
+// against 45.1 us with one, while one is fastest for the embed: 101.4 us
+// against 114.7 us with two and 148.5 us with four).
+constexpr int kEmbedAllBytesUnits = 1;
+constexpr int kExtractAllBytesUnits = 4;
+template <int CH, bool EMBED>
+__host__ __device__ constexpr int units_per_iter()
+{
+    return CH == 1 ? (EMBED ? kEmbedAllBytesUnits : kExtractAllBytesUnits) : 1;
+}
+
+// Embed over units (cover and stego 16-byte aligned): U units per thread
+// per iteration (lane-interleaved), each unit's 16K stream bits = stream
+// bytes [2Ku, 2Ku + 2K) loaded as one big-endian word, all loads issued
+// before any arithmetic.  Units wholly past the stream are copied.
+// Carrying bytes after the last whole unit (fewer than 16) are done by
+// block 0 byte by byte.
+template <int K, int CH, int PLANE, bool STATS>
+__global__ void __launch_bounds__(512) embedk_units(KView a)
+{
+    constexpr int U = units_per_iter<CH, true>();
     constexpr uint32_t MASK = (1u << K) - 1u;
     constexpr uint32_t BYTEMASK = MASK * 0x01010101u;
     unsigned long long changed = 0, sse = 0;
     embed_res(a, STATS);
-    const uint64_t nvec = a.n_carry >> 4;
-    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover);
-    uint4 *dst = reinterpret_cast<uint4 *>(a.stego);
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * V;
-    for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x; v0 < nvec;
-         v0 += stride) {
-        uint4 c[V];
-        uint64_t X[V];
+    const uint64_t nunits = a.n_carry >> 4;
+    for (uint64_t u0 = (uint64_t)blockIdx.x * blockDim.x * U + threadIdx.x; u0 < nunits;
+         u0 += (uint64_t)gridDim.x * blockDim.x * U) {
+        uint32_t w[U][4 * CH];
+        uint64_t X[U];
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
-            if (v < nvec)
-                c[u] = __ldcs(src + v);
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            if (u < nunits)
+                load_unit<CH>(a.cover, u, w[r]);
         }
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
-            X[u] = 0;
-            if (v < nvec && (v + 1) * 16u * K <= a.t_bits)
-                X[u] = stream_window<K>(a, v);
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            X[r] = (u < nunits && (u + 1) * 16u * K <= a.t_bits) ? stream_window<K>(a, u) : 0ull;
         }
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
-            if (v >= nvec)
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            if (u >= nunits)
                 continue;
-            uint4 o = c[u];
-            const uint64_t b0 = v * 16u * K; // first stream bit of the vector
-            if (b0 + 16u * K <= a.t_bits) {
-                uint32_t f[4];
+            const uint64_t b0 = u * 16u * K; // first stream bit of the unit
+            if (b0 < a.t_bits) {
+                uint32_t c[4], o[4];
+                gather_unit<CH, PLANE>(w[r], c);
+                if (b0 + 16u * K <= a.t_bits) {
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    f[w] = 0;
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        const int t = 4 * w + l;
-                        f[w] |= (uint32_t)((X[u] >> (64 - K * (t + 1))) & MASK) << (8 * l);
-                    }
+                    for (int i = 0; i < 4; ++i)
+                        o[i] = (c[i] & ~BYTEMASK) | unit_fields<K>(X[r], i);
+                } else {
+                    const uint4 e = stream_end_vector(a, u, make_uint4(c[0], c[1], c[2], c[3]));
+                    o[0] = e.x;
+                    o[1] = e.y;
+                    o[2] = e.z;
+                    o[3] = e.w;
                 }
-                o.x = (c[u].x & ~BYTEMASK) | f[0];
-                o.y = (c[u].y & ~BYTEMASK) | f[1];
-                o.z = (c[u].z & ~BYTEMASK) | f[2];
-                o.w = (c[u].w & ~BYTEMASK) | f[3];
-            } else if (b0 < a.t_bits) {
-                o = stream_end_vector(a, v, c[u]);
+                uint32_t d[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    d[i] = o[i] ^ c[i];
+                    if (STATS)
+                        low_stats(o[i], c[i], changed, sse);
+                }
+                scatter_xor<CH, PLANE>(w[r], d);
             }
-            __stcs(dst + v, o);
-            if (STATS) {
-                low_stats(o.x, c[u].x, changed, sse);
-                low_stats(o.y, c[u].y, changed, sse);
-                low_stats(o.z, c[u].z, changed, sse);
-                low_stats(o.w, c[u].w, changed, sse);
-            }
+            store_unit<CH>(a.stego, u, w[r]);
         }
     }
-    // carrying bytes after the last whole vector
-    if (blockIdx.x == 0 && threadIdx.x < (uint32_t)(a.n_carry & 15u)) {
-        const uint64_t x = ((a.n_carry >> 4) << 4) + threadIdx.x;
-        uint32_t fv, fm;
-        field_of(a, x, fv, fm);
-        const uint32_t cb = a.cover[x];
-        const uint32_t ob = (cb & ~fm) | (fv & fm);
-        a.stego[x] = (uint8_t)ob;
+    // cover bytes of the carrying bytes after the last whole unit: plane
+    // bytes take their field, the other bytes of those pixels are copied
+    if (blockIdx.x == 0 && threadIdx.x < (uint32_t)(a.n_carry & 15u) * CH) {
+        const uint64_t pbyte = ((a.n_carry >> 4) << 4) * CH + threadIdx.x;
+        const uint32_t cb = a.cover[pbyte];
+        uint32_t ob = cb;
+        if (threadIdx.x % CH == PLANE) {
+            uint32_t fv, fm;
+            field_of(a, pbyte / CH, fv, fm);
+            ob = (cb & ~fm) | (fv & fm);
+        }
+        a.stego[pbyte] = (uint8_t)ob;
         if (STATS) {
-            const uint32_t d = ob > cb ? ob - cb : cb - ob;
-            changed += d != 0;
-            sse += d * d;
+            const uint32_t dd = ob > cb ? ob - cb : cb - ob;
+            changed += dd != 0;
+            sse += dd * dd;
         }
     }
     if (STATS)
@@ -298,22 +455,20 @@ __device__ __forceinline__ int extractk_prologue(const KView &a, uint64_t &len)
     return status;
 }
 
-// All bytes, aligned stego: vector v yields stream bytes [2Kv, 2Kv + 2K).
-template <int K>
-__global__ void __launch_bounds__(512) extractk_vec(KView a)
+// Extract over units (stego 16-byte aligned): unit u yields stream bytes
+// [2Ku, 2Ku + 2K); U units per thread per iteration, loads first.  Stream
+// bytes past the last whole unit go bit by bit.
+template <int K, int CH, int PLANE>
+__global__ void __launch_bounds__(512) extractk_units(KView a)
 {
-    constexpr uint32_t MASK = (1u << K) - 1u;
     uint64_t len;
     if (extractk_prologue(a, len) != STEGO_OK)
         return;
     const uint64_t hb = a.header ? 4u : 0u;       // stream bytes before the message
     const uint64_t sbytes = len + hb;              // stream bytes to recover
-    // whole 16-byte vectors of the stego only; the stream bytes after them
-    // (when the stego's length is not a multiple of 16) go bit by bit
     const uint64_t want = (sbytes + 2 * K - 1) / (2 * K);
-    const uint64_t nvec = want < (a.C >> 4) ? want : (a.C >> 4);
-    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover);
-    for (uint64_t q = 2u * K * nvec + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nunits = want < (a.n_carry >> 4) ? want : (a.n_carry >> 4);
+    for (uint64_t q = 2u * K * nunits + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
          q < sbytes; q += (uint64_t)gridDim.x * blockDim.x) {
         if (q < hb)
             continue;
@@ -323,28 +478,40 @@ __global__ void __launch_bounds__(512) extractk_vec(KView a)
             v |= stream_bit(a, 8u * q + i) << (7 - i);
         a.out[q - hb] = (uint8_t)v;
     }
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 c = __ldcs(src + v);
-        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
-        uint64_t X = 0;
+    constexpr int U = units_per_iter<CH, false>();
+    for (uint64_t u0 = (uint64_t)blockIdx.x * blockDim.x * U + threadIdx.x; u0 < nunits;
+         u0 += (uint64_t)gridDim.x * blockDim.x * U) {
+        uint32_t w[U][4 * CH];
 #pragma unroll
-        for (int t = 0; t < 16; ++t)
-            X |= (uint64_t)((w[t >> 2] >> (8 * (t & 3))) & MASK) << (64 - K * (t + 1));
-        const uint64_t q0 = 2u * K * v; // first stream byte of the vector
-        uint8_t *op = a.out + (q0 - hb);
-        if ((K & 1) == 0 && q0 >= hb && q0 + 2 * K <= sbytes && (((uintptr_t)op & 3u) == 0)) {
-            // message bytes only, 4-byte aligned: K/2 word stores
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            if (u < nunits)
+                load_unit<CH>(a.cover, u, w[r]);
+        }
 #pragma unroll
-            for (int i = 0; i < K / 2; ++i)
-                reinterpret_cast<uint32_t *>(op)[i] =
-                    __byte_perm((uint32_t)(X >> (32 - 32 * i)), 0u, 0x0123u);
-        } else {
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            if (u >= nunits)
+                continue;
+            uint32_t g[4];
+            gather_unit<CH, PLANE>(w[r], g);
+            const uint64_t X = unit_window<K>(g);
+            const uint64_t q0 = 2u * K * u; // first stream byte of the unit
+            uint8_t *op = a.out + (q0 - hb);
+            if ((K & 1) == 0 && q0 >= hb && q0 + 2 * K <= sbytes &&
+                (((uintptr_t)op & 3u) == 0)) {
+                // message bytes only, 4-byte aligned: K/2 word stores
 #pragma unroll
-            for (int i = 0; i < 2 * K; ++i) {
-                const uint64_t q = q0 + i; // stream byte
-                if (q >= hb && q < sbytes)
-                    a.out[q - hb] = (uint8_t)(X >> (56 - 8 * i));
+                for (int i = 0; i < K / 2; ++i)
+                    reinterpret_cast<uint32_t *>(op)[i] =
+                        __byte_perm((uint32_t)(X >> (32 - 32 * i)), 0u, 0x0123u);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 2 * K; ++i) {
+                    const uint64_t q = q0 + i; // stream byte
+                    if (q >= hb && q < sbytes)
+                        a.out[q - hb] = (uint8_t)(X >> (56 - 8 * i));
+                }
             }
         }
     }
@@ -380,6 +547,73 @@ __global__ void __launch_bounds__(512) extractk_bytes(KView a)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Unit kernels exist for 1, 3 and 4 channels.
+bool unit_layout(bool plane_only, const stego_geom *g)
+{
+    return !plane_only || g->channels == 1 || g->channels == 3 || g->channels == 4;
+}
+
+template <int K, bool STATS>
+const void *embed_units_for(uint32_t ch, uint32_t plane)
+{
+    if (ch == 1)
+        return (const void *)embedk_units<K, 1, 0, STATS>;
+    if (ch == 3) {
+        switch (plane) {
+        case 0: return (const void *)embedk_units<K, 3, 0, STATS>;
+        case 1: return (const void *)embedk_units<K, 3, 1, STATS>;
+        default: return (const void *)embedk_units<K, 3, 2, STATS>;
+        }
+    }
+    switch (plane) {
+    case 0: return (const void *)embedk_units<K, 4, 0, STATS>;
+    case 1: return (const void *)embedk_units<K, 4, 1, STATS>;
+    case 2: return (const void *)embedk_units<K, 4, 2, STATS>;
+    default: return (const void *)embedk_units<K, 4, 3, STATS>;
+    }
+}
+
+template <bool STATS>
+const void *embed_units_kernel(uint32_t k, uint32_t ch, uint32_t plane)
+{
+    switch (k) {
+    case 1: return embed_units_for<1, STATS>(ch, plane);
+    case 2: return embed_units_for<2, STATS>(ch, plane);
+    case 3: return embed_units_for<3, STATS>(ch, plane);
+    default: return embed_units_for<4, STATS>(ch, plane);
+    }
+}
+
+template <int K>
+const void *extract_units_for(uint32_t ch, uint32_t plane)
+{
+    if (ch == 1)
+        return (const void *)extractk_units<K, 1, 0>;
+    if (ch == 3) {
+        switch (plane) {
+        case 0: return (const void *)extractk_units<K, 3, 0>;
+        case 1: return (const void *)extractk_units<K, 3, 1>;
+        default: return (const void *)extractk_units<K, 3, 2>;
+        }
+    }
+    switch (plane) {
+    case 0: return (const void *)extractk_units<K, 4, 0>;
+    case 1: return (const void *)extractk_units<K, 4, 1>;
+    case 2: return (const void *)extractk_units<K, 4, 2>;
+    default: return (const void *)extractk_units<K, 4, 3>;
+    }
+}
+
+const void *extract_units_kernel(uint32_t k, uint32_t ch, uint32_t plane)
+{
+    switch (k) {
+    case 1: return extract_units_for<1>(ch, plane);
+    case 2: return extract_units_for<2>(ch, plane);
+    case 3: return extract_units_for<3>(ch, plane);
+    default: return extract_units_for<4>(ch, plane);
+    }
+}
+
 } // namespace
 
 cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t k, bool plane_only,
@@ -406,17 +640,16 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     const uint64_t t_carry = (a.t_bits + k - 1) / k; // carrying bytes the stream uses
     const int T = sh.threads;
     void *args[] = {&a};
-    if (!plane_only && aligned16(cover) && aligned16(stego)) {
-        a.n_carry = inplace ? t_carry : C;
-        const void *kern;
-        switch (k) {
-        case 2: kern = stats ? (const void *)embedk_vec<2, true> : (const void *)embedk_vec<2, false>; break;
-        case 3: kern = stats ? (const void *)embedk_vec<3, true> : (const void *)embedk_vec<3, false>; break;
-        default: kern = stats ? (const void *)embedk_vec<4, true> : (const void *)embedk_vec<4, false>; break;
-        }
-        const uint64_t nvec = a.n_carry >> 4;
-        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nvec ? nvec : 1,
-                                         (uint64_t)T); // one vector per thread
+    if (aligned16(cover) && aligned16(stego) && unit_layout(plane_only, g)) {
+        // carrying bytes processed: all of them out of place (the rest of
+        // the cover is copied with them), those the stream uses in place
+        a.n_carry = inplace ? t_carry : (plane_only ? (uint64_t)g->width * g->height : C);
+        const void *kern = stats ? embed_units_kernel<true>(k, a.channels, a.plane)
+                                 : embed_units_kernel<false>(k, a.channels, a.plane);
+        const uint64_t nunits = a.n_carry >> 4;
+        const int per_thread = a.channels == 1 ? kEmbedAllBytesUnits : 1;
+        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nunits ? nunits : 1,
+                                         (uint64_t)T * per_thread);
         return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
     }
     if (plane_only && !inplace) {
@@ -459,15 +692,12 @@ cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_onl
     }
     const int T = sh.threads;
     void *args[] = {&a};
-    if (!plane_only && aligned16(st)) {
-        const void *kern;
-        switch (k) {
-        case 2: kern = (const void *)extractk_vec<2>; break;
-        case 3: kern = (const void *)extractk_vec<3>; break;
-        default: kern = (const void *)extractk_vec<4>; break;
-        }
-        const uint64_t nvec = (max_len + 4 + 2 * k - 1) / (2 * k);
-        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nvec ? nvec : 1, (uint64_t)T);
+    if (aligned16(st) && unit_layout(plane_only, g)) {
+        const void *kern = extract_units_kernel(k, a.channels, a.plane);
+        const uint64_t nunits = (max_len + 4 + 2 * k - 1) / (2 * k);
+        const int per_thread = a.channels == 1 ? kExtractAllBytesUnits : 1;
+        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nunits ? nunits : 1,
+                                         (uint64_t)T * per_thread);
         return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
     }
     const void *kern = (const void *)extractk_bytes;

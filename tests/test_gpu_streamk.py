@@ -145,3 +145,58 @@ def test_full_size_8192(S, O, k):
     res2 = S.new_result()
     S.stego_extract(stego, out, 0, S.BITS(k) | S.HEADER_BE32, res2)
     assert S.read_result(res2)["msg_bytes"] == m and torch.equal(out, msg)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("cp", [(3, 0), (3, 1), (3, 2), (4, 0), (4, 1), (4, 2), (4, 3)])
+def test_one_plane_units(S, O, k, cp):
+    """Every (channels, plane) of the 16-pixel unit kernels over many units
+    (and grid-stride iterations) with a ragged tail of 5 pixels."""
+    Cc, p = cp
+    geom = (129, 37, Cc, p)   # 4773 pixels = 298 units + 5
+    rng = np.random.default_rng(1000 * k + 10 * Cc + p)
+    cover = rng.integers(0, 256, 129 * 37 * Cc, dtype=np.uint8)
+    for header in (True, False):
+        cap = S.stego_capacity(cover.size, _flags(S, k, header, geom), geom=geom)
+        for m in sorted({cap // 3, cap - 1, cap}):
+            msg = rng.integers(0, 256, m, dtype=np.uint8)
+            for inplace in (False, True):
+                _check(S, O, cover, msg, k, header, geom=geom, inplace=inplace)
+
+
+@pytest.mark.parametrize("offs", [(3, 7, 1), (0, 16, 2), (5, 5, 0)])
+def test_one_plane_misaligned(S, O, offs):
+    geom = (64, 9, 3, 1)
+    rng = np.random.default_rng(sum(offs))
+    cover = rng.integers(0, 256, 64 * 9 * 3, dtype=np.uint8)
+    for k in (1, 2, 3):
+        cap = S.stego_capacity(cover.size, _flags(S, k, True, geom), geom=geom)
+        msg = rng.integers(0, 256, cap // 2, dtype=np.uint8)
+        _check(S, O, cover, msg, k, True, geom=geom, offs=offs)
+
+
+def test_full_size_8192_plane0(S, O):
+    """The 8192x8192x3 cover, k = 2 on plane 0 at full capacity (the bench
+    leg's workload), every byte against the oracle."""
+    from paper_0912_0947_gb300 import synth
+    C = 8192 * 8192 * 3
+    geom = (8192, 8192, 3, 0)
+    flags = S.BITS(2) | S.HEADER_BE32 | S.PLANE_ONLY
+    cover = synth.uniform_bytes(C, 0xC0FFEE51, "cuda")
+    m = S.stego_capacity(C, flags, geom=geom)
+    msg = synth.uniform_bytes(m, 0xC0FFEE52, "cuda")
+    stego = torch.empty_like(cover)
+    res = S.new_result()
+    S.stego_embed(cover, stego, msg, flags | S.FUSE_STATS, res, geom=geom)
+    c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+    st, want = O.streamk_embed(c_h, m_h, 2, header=True, geom=geom)
+    assert st == 0 and np.array_equal(stego.cpu().numpy(), want)
+    r = S.read_result(res)
+    assert (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+    out = torch.empty(m, dtype=torch.uint8, device="cuda")
+    res2 = S.new_result()
+    S.stego_extract(stego, out, 0, flags, res2, geom=geom)
+    assert S.read_result(res2)["msg_bytes"] == m and torch.equal(out, msg)
+    buf = cover.clone()
+    S.stego_embed(buf, buf, msg, flags, geom=geom)
+    assert torch.equal(buf, stego)
