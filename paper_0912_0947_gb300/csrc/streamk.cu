@@ -45,6 +45,10 @@ struct KView {
     uint32_t channels, plane;
     stego_result *res;
     uint64_t res_msg_bytes;
+    uint64_t full_units;  // embed: units wholly inside the stream, t_bits / 16k
+    uint64_t part_units;  // embed: units touching the stream, ceil(t_bits / 16k)
+    uint32_t msg_w4;      // embed: msg - (header bytes) is 4-byte aligned
+    uint32_t pad;
 };
 
 __device__ __forceinline__ uint64_t carry_pos(const KView &a, uint64_t x)
@@ -95,15 +99,35 @@ __device__ __forceinline__ void embed_res(const KView &a, bool stats)
     }
 }
 
-// Changed bytes and squared error of a word pair that differs only in the
-// low four bits of some bytes.
-__device__ __forceinline__ void low_stats(uint32_t o, uint32_t c, unsigned long long &changed,
-                                          unsigned long long &sse)
+// Changed bytes and squared error of a unit's 16 carrying bytes (c before,
+// o after, d = o ^ c, differences in the low K bits only), summed in 32 bits
+// per unit.  A byte changed when any of its low K bits did: the K bits are
+// folded into bit 0 and the four words' flags packed into one word for one
+// population count.  With K = 1 every change is +-1, so the squared error
+// equals the count.
+template <int K>
+__device__ __forceinline__ void unit_stats(const uint32_t (&o)[4], const uint32_t (&c)[4],
+                                           const uint32_t (&d)[4], unsigned long long &changed,
+                                           unsigned long long &sse)
 {
-    const uint32_t x = o ^ c;
-    changed += __popc((x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x01010101u);
-    const uint32_t d = __vabsdiffu4(o & 0x0F0F0F0Fu, c & 0x0F0F0F0Fu);
-    sse += __dp4a(d, d, 0u);
+    constexpr uint32_t BM = ((1u << K) - 1u) * 0x01010101u;
+    uint32_t flags = 0, s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        uint32_t f = d[i];
+        if (K > 1)
+            f |= f >> 1;
+        if (K > 2)
+            f |= f >> 2; // bits 0..3 of each byte folded for K = 3, 4
+        flags |= (f & 0x01010101u) << i;
+        if (K > 1) {
+            const uint32_t ad = __vabsdiffu4(o[i] & BM, c[i] & BM);
+            s = __dp4a(ad, ad, s);
+        }
+    }
+    const uint32_t n = __popc(flags);
+    changed += n;
+    sse += K > 1 ? s : n;
 }
 
 // The one vector where the stream ends, field by field (a call of its own
@@ -130,7 +154,8 @@ __device__ __forceinline__ uint64_t stream_window(const KView &a, uint64_t v)
     const uint64_t q0 = 2u * K * v;
     const uint64_t hb = a.header ? 4u : 0u;
     const uint8_t *mp = a.msg + (q0 - hb);
-    if ((K & 1) == 0 && q0 >= hb && (((uintptr_t)mp & 3u) == 0)) {
+    // q0 is a multiple of 4 for even K, so mp's alignment is the launch's
+    if ((K & 1) == 0 && q0 >= hb && a.msg_w4) {
 #pragma unroll
         for (int i = 0; i < K / 2; ++i) {
             const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(mp) + i);
@@ -326,18 +351,17 @@ __global__ void __launch_bounds__(512) embedk_units(KView a)
 #pragma unroll
         for (int r = 0; r < U; ++r) {
             const uint64_t u = u0 + (uint64_t)r * blockDim.x;
-            X[r] = (u < nunits && (u + 1) * 16u * K <= a.t_bits) ? stream_window<K>(a, u) : 0ull;
+            X[r] = (u < nunits && u < a.full_units) ? stream_window<K>(a, u) : 0ull;
         }
 #pragma unroll
         for (int r = 0; r < U; ++r) {
             const uint64_t u = u0 + (uint64_t)r * blockDim.x;
             if (u >= nunits)
                 continue;
-            const uint64_t b0 = u * 16u * K; // first stream bit of the unit
-            if (b0 < a.t_bits) {
+            if (u < a.part_units) {
                 uint32_t c[4], o[4];
                 gather_unit<CH, PLANE>(w[r], c);
-                if (b0 + 16u * K <= a.t_bits) {
+                if (u < a.full_units) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
                         o[i] = (c[i] & ~BYTEMASK) | unit_fields<K>(X[r], i);
@@ -350,11 +374,10 @@ __global__ void __launch_bounds__(512) embedk_units(KView a)
                 }
                 uint32_t d[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 4; ++i)
                     d[i] = o[i] ^ c[i];
-                    if (STATS)
-                        low_stats(o[i], c[i], changed, sse);
-                }
+                if (STATS)
+                    unit_stats<K>(o, c, d, changed, sse);
                 scatter_xor<CH, PLANE>(w[r], d);
             }
             store_unit<CH>(a.stego, u, w[r]);
@@ -636,6 +659,9 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     a.plane = plane_only ? g->plane : 0u;
     a.res = res;
     a.res_msg_bytes = m;
+    a.full_units = a.t_bits / (16u * k);
+    a.part_units = (a.t_bits + 16u * k - 1) / (16u * k);
+    a.msg_w4 = (((uintptr_t)msg - (header ? 4u : 0u)) & 3u) == 0;
     const bool inplace = cover == stego;
     const uint64_t t_carry = (a.t_bits + k - 1) / k; // carrying bytes the stream uses
     const int T = sh.threads;
