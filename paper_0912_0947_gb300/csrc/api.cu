@@ -23,6 +23,13 @@ Shape g_shape[STEGO_OP_COUNT] = {
 };
 int g_sms[kMaxDevices];
 
+// Statistics slots: per device, the streams that own slots 0..n-1 and the
+// device address of the slot array.
+constexpr int kStatSlots = 256;
+cudaStream_t g_slot_stream[kMaxDevices][kStatSlots];
+int g_slot_n[kMaxDevices];
+StatSlot *g_slot_base[kMaxDevices];
+
 struct OccEntry {
     const void *kernel;
     int threads;
@@ -158,6 +165,40 @@ cudaError_t write_result(stego_result *res, uint64_t msg_bytes, int status, cuda
 
 } // namespace stego
 
+// Zero at load; each slot is cleared again by the last CTA of every launch
+// that used it.
+static __device__ stego::StatSlot g_stat_slots[stego::kStatSlots];
+
+namespace stego {
+
+StatSlot *stats_slot(cudaStream_t s)
+{
+    if (s == cudaStreamPerThread)
+        return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_slot_base[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_stat_slots) != cudaSuccess || !p)
+            return nullptr;
+        g_slot_base[dev] = static_cast<StatSlot *>(p);
+    }
+    for (int i = 0; i < g_slot_n[dev]; ++i)
+        if (g_slot_stream[dev][i] == s)
+            return g_slot_base[dev] + i;
+    if (g_slot_n[dev] == kStatSlots)
+        return nullptr;
+    g_slot_stream[dev][g_slot_n[dev]] = s;
+    return g_slot_base[dev] + g_slot_n[dev]++;
+}
+
+} // namespace stego
+
 using namespace stego;
 
 extern "C" {
@@ -260,7 +301,9 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
 
     cudaStream_t s = (cudaStream_t)stream;
     const Shape sh = shape_for(STEGO_OP_EMBED, nullptr);
-    if (stats && cudaMemsetAsync(d_result, 0, 2 * sizeof(uint64_t), s) != cudaSuccess)
+    // fused statistics: the stream's slot, or zeroed result fields
+    StatSlot *slot = stats ? stats_slot(s) : nullptr;
+    if (stats && !slot && cudaMemsetAsync(d_result, 0, 2 * sizeof(uint64_t), s) != cudaSuccess)
         return STEGO_E_CUDA;
 
     if (layout == STEGO_LAYOUT_STREAM1 && (k != 1 || plane_only)) {
@@ -270,7 +313,7 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
             return STEGO_OK;
         }
         return cuda_status(sk_embed(d_cover, d_stego, cover_bytes, k, plane_only, geom, d_msg,
-                                    msg_bytes, header, stats, d_result, sh, s));
+                                    msg_bytes, header, stats, d_result, sh, s, slot));
     }
     if (layout == STEGO_LAYOUT_STREAM1) {
         const uint64_t slen = msg_bytes + (header ? 4u : 0u);
@@ -282,12 +325,13 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
             return STEGO_OK;
         }
         return cuda_status(s1_embed(d_cover, d_stego, n, T, d_msg, slen, header,
-                                    (uint32_t)(8u * msg_bytes), stats, d_result, msg_bytes, sh, s));
+                                    (uint32_t)(8u * msg_bytes), stats, d_result, msg_bytes, sh, s,
+                                    slot));
     }
     // PAPER2 out of place: one fused pass when the layout allows it
     if (!inplace && cover_bytes > 0 && p2_fused_ok(d_cover, d_stego, *geom))
         return cuda_status(p2_embed_fused(d_cover, d_stego, *geom, d_msg, msg_bytes, stats,
-                                          d_result, sh, s));
+                                          d_result, sh, s, slot));
     // otherwise copy the cover (out of place), then write the 4N carrying bytes
     if (!inplace && cover_bytes > 0) {
         cudaError_t e = s1_embed(d_cover, d_stego, cover_bytes, 0, nullptr, 0, false, 0, false,
@@ -302,7 +346,8 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
             return cuda_status(write_result(d_result, 0, STEGO_OK, s));
         return STEGO_OK;
     }
-    return cuda_status(p2_embed(d_cover, d_stego, *geom, d_msg, msg_bytes, stats, d_result, sh, s));
+    return cuda_status(p2_embed(d_cover, d_stego, *geom, d_msg, msg_bytes, stats, d_result, sh, s,
+                                slot));
 }
 
 int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
@@ -460,6 +505,7 @@ static_assert(sizeof(stego_desc) == 72, "stego_desc layout");
 static_assert(sizeof(stego_result) == 32, "stego_result layout");
 static_assert(sizeof(stego_geom) == 16, "stego_geom layout");
 static_assert(sizeof(stego_tune) == 16, "stego_tune layout");
+static_assert(sizeof(stego::StatSlot) == 32, "statistics slot layout");
 static_assert(sizeof(stego_request) == 64, "stego_request layout");
 static_assert(sizeof(stego_completion) == 64, "stego_completion layout");
 static_assert(sizeof(stego_server_config) == 48, "stego_server_config layout");

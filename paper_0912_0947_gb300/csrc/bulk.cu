@@ -220,6 +220,7 @@ struct BulkEmbedArgs {
     s1::EmbedView a;
     stego_result *res;
     uint64_t res_msg_bytes;
+    StatSlot *slot;
     uint32_t stages;
     uint32_t pad;
 };
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(512) embed_bulk(BulkEmbedArgs e)
     if (blockIdx.x == 0)
         s1::embed_tail<STATS>(a, changed, sse);
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&e.res->changed));
+        block_stats(changed, sse, e.res, e.slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,7 +486,7 @@ uint32_t bulk_stages(const Shape &sh)
 cudaError_t s1_embed_bulk(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes,
                           uint64_t t_bytes, const uint8_t *msg, uint64_t slen, bool header,
                           uint32_t nbits, bool stats, stego_result *res, uint64_t res_msg_bytes,
-                          const Shape &sh, cudaStream_t s)
+                          const Shape &sh, cudaStream_t s, StatSlot *slot)
 {
     BulkEmbedArgs e;
     e.a.cover = cover;
@@ -500,6 +501,7 @@ cudaError_t s1_embed_bulk(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes
     e.a.pad = 0;
     e.res = res;
     e.res_msg_bytes = res_msg_bytes;
+    e.slot = stats ? slot : nullptr;
     e.stages = bulk_stages(sh);
     e.pad = 0;
     const int v = clamp_v(sh.vec);

@@ -38,6 +38,29 @@ int persistent_grid(const void *kernel, int threads, size_t smem, int ctas_per_s
                     uint64_t units, uint64_t units_per_cta);
 
 // ---------------------------------------------------------------------------
+// Fused statistics without a zeroing copy
+// ---------------------------------------------------------------------------
+
+// Accumulator of one launch's changed-byte count and squared error, one per
+// stream (a static device array, zero at load).  Every CTA adds its partial
+// totals and then takes a ticket; the CTA with the last ticket moves the
+// totals into the result and clears the slot for the stream's next launch.
+struct StatSlot {
+    unsigned long long changed;
+    unsigned long long sse;
+    unsigned int arrived;
+    unsigned int pad;
+    unsigned long long pad2;
+};
+
+// The slot of stream s on the current device, or nullptr: then the caller
+// zeroes res->changed/sse before the launch and the CTAs add into them.
+// nullptr for streams being captured into a graph (a replay may run beside
+// direct calls on the same stream), for the per-thread default stream
+// (one handle, several streams) and once every slot is taken.
+StatSlot *stats_slot(cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Launchers (all stream-ordered, no synchronisation).  They return the CUDA
 // error of the launch.  `res` (nullable) receives msg_bytes = res_msg_bytes
 // and status STEGO_OK from block 0 of the launch; with `stats`, res->changed
@@ -50,7 +73,8 @@ int persistent_grid(const void *kernel, int threads, size_t smem, int ctas_per_s
 // (message plus 4 header bytes when `header`).  nbits: the header value.
 cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uint64_t t_bytes,
                      const uint8_t *msg, uint64_t slen, bool header, uint32_t nbits, bool stats,
-                     stego_result *res, uint64_t res_msg_bytes, const Shape &sh, cudaStream_t s);
+                     stego_result *res, uint64_t res_msg_bytes, const Shape &sh, cudaStream_t s,
+                     StatSlot *slot = nullptr);
 
 // STREAM1 extract.  With `header`, the length comes from the stego and all
 // fields of `res` (required) are written by block 0; otherwise raw_len bytes
@@ -63,7 +87,7 @@ cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap
 // it carries: out of place the caller has copied the cover into stego first.
 cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
                      const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
-                     const Shape &sh, cudaStream_t s);
+                     const Shape &sh, cudaStream_t s, StatSlot *slot = nullptr);
 cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uint64_t N,
                        stego_result *res, const Shape &sh, cudaStream_t s);
 
@@ -73,13 +97,14 @@ cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uin
 bool p2_fused_ok(const uint8_t *cover, const uint8_t *stego, const stego_geom &g);
 cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
                            const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
-                           const Shape &sh, cudaStream_t s);
+                           const Shape &sh, cudaStream_t s, StatSlot *slot = nullptr);
 
 // STREAM1 with k = 1..4 bits per carrying byte, over all bytes or one plane
 // (k >= 2 or plane_only; k = 1 over all bytes is s1_embed).
 cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t k, bool plane_only,
                      const stego_geom *g, const uint8_t *msg, uint64_t m, bool header,
-                     bool stats, stego_result *res, const Shape &sh, cudaStream_t s);
+                     bool stats, stego_result *res, const Shape &sh, cudaStream_t s,
+                     StatSlot *slot = nullptr);
 cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_only,
                        const stego_geom *g, uint8_t *msg, uint64_t cap, uint64_t raw_len,
                        bool header, stego_result *res, const Shape &sh, cudaStream_t s);
@@ -92,7 +117,7 @@ uint32_t bulk_stages(const Shape &sh);
 cudaError_t s1_embed_bulk(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes,
                           uint64_t t_bytes, const uint8_t *msg, uint64_t slen, bool header,
                           uint32_t nbits, bool stats, stego_result *res, uint64_t res_msg_bytes,
-                          const Shape &sh, cudaStream_t s);
+                          const Shape &sh, cudaStream_t s, StatSlot *slot = nullptr);
 cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
                             uint64_t raw_len, bool header, stego_result *res, const Shape &sh,
                             cudaStream_t s);
@@ -140,6 +165,51 @@ __device__ __forceinline__ void block_add2(unsigned long long a, unsigned long l
                 atomicAdd(out, a);
             if (b)
                 atomicAdd(out + 1, b);
+        }
+    }
+}
+
+// The statistics of a single-cover launch: the block's totals go into
+// res->changed/sse (zeroed by the caller) without a slot, or into the slot,
+// whose last arriving CTA writes res->changed/sse.  All threads of every
+// CTA of the grid must call it once.
+__device__ __forceinline__ void block_stats(unsigned long long a, unsigned long long b,
+                                            stego_result *res, StatSlot *slot)
+{
+    if (!slot) {
+        block_add2(a, b, reinterpret_cast<unsigned long long *>(&res->changed));
+        return;
+    }
+    __shared__ unsigned long long sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = 0;
+        b = 0;
+        for (int i = 0; i < nw; ++i) {
+            a += sa[i];
+            b += sb[i];
+        }
+        if (a)
+            atomicAdd(&slot->changed, a);
+        if (b)
+            atomicAdd(&slot->sse, b);
+        __threadfence(); // the adds are visible before the ticket
+        if (atomicAdd(&slot->arrived, 1u) == gridDim.x - 1) {
+            __threadfence();
+            res->changed = atomicExch(&slot->changed, 0ull);
+            res->sse = atomicExch(&slot->sse, 0ull);
+            atomicExch(&slot->arrived, 0u);
         }
     }
 }

@@ -19,6 +19,7 @@ using p2::View;
 struct P2Args {
     View v;
     stego_result *res;
+    StatSlot *slot;
 };
 
 __device__ __forceinline__ void write_res(const P2Args &a, bool stats)
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(kUnitThreads, 3) p2_embed_units(P2Args a)
         a.v, blockIdx.x * blockDim.x * kUnitsPerThread + threadIdx.x, nunits,
         gridDim.x * blockDim.x * kUnitsPerThread, changed, sse);
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&a.res->changed));
+        block_stats(changed, sse, a.res, a.slot);
 }
 
 template <bool STATS>
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(512, 2) p2_embed_rows(P2Args a)
     write_res(a, STATS);
     p2::rows_embed<STATS>(a.v, blockIdx.x, a.v.R, gridDim.x, changed, sse);
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&a.res->changed));
+        block_stats(changed, sse, a.res, a.slot);
 }
 
 __device__ __forceinline__ void extract_res(const P2Args &a)
@@ -92,6 +93,7 @@ P2Args make_args(const uint8_t *src, uint8_t *dst, const stego_geom &g, const ui
     P2Args a;
     a.v = p2::make_view(src, dst, g.width, g.height, g.channels, g.plane, msg_in, msg_out, N);
     a.res = res;
+    a.slot = nullptr;
     return a;
 }
 
@@ -151,9 +153,10 @@ bool p2_fused_ok(const uint8_t *cover, const uint8_t *stego, const stego_geom &g
 
 cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
                            const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
-                           const Shape &sh, cudaStream_t s)
+                           const Shape &sh, cudaStream_t s, StatSlot *slot)
 {
     P2Args a = make_args(cover, stego, g, msg, nullptr, N, res);
+    a.slot = stats ? slot : nullptr;
     const void *k = stats ? units_kernel<true>(g.channels, g.plane)
                           : units_kernel<false>(g.channels, g.plane);
     const uint64_t nunits = (uint64_t)(g.width / 16u) * g.height;
@@ -165,9 +168,10 @@ cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geo
 
 cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
                      const uint8_t *msg, uint64_t N, bool stats, stego_result *res,
-                     const Shape &sh, cudaStream_t s)
+                     const Shape &sh, cudaStream_t s, StatSlot *slot)
 {
     P2Args a = make_args(cover, stego, g, msg, nullptr, N, res);
+    a.slot = stats ? slot : nullptr;
     const void *k = stats ? (const void *)p2_embed_rows<true> : (const void *)p2_embed_rows<false>;
     const int grid = row_grid(k, sh, a.v.R);
     void *args[] = {&a};

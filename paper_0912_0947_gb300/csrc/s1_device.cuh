@@ -123,6 +123,9 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
 {
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover);
     uint4 *dst = reinterpret_cast<uint4 *>(a.stego);
+    // changed bytes of this call in 32 bits: a thread covers at most
+    // (bytes / threads) bytes, far below 2^32 for any cover in device memory
+    uint32_t n = 0;
     for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
         uint4 c[V];
         uint32_t p[V];
@@ -139,7 +142,6 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
             if (v < v_end && (v << 4) < a.t_bytes)
                 p[u] = stream_pair(a, v << 1);
         }
-        uint32_t n = 0;
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const uint64_t v = v0 + (uint64_t)u * blockDim.x;
@@ -147,10 +149,10 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
                 continue;
             __stcs(dst + v, embed_vec16<STATS>(a, v, c[u], p[u], n));
         }
-        if (STATS) {
-            changed += n;
-            sse += n;
-        }
+    }
+    if (STATS) {
+        changed += n;
+        sse += n;
     }
 }
 

@@ -21,6 +21,7 @@ struct EmbedArgs {
     EmbedView a;
     stego_result *res;
     uint64_t res_msg_bytes;
+    StatSlot *slot;
 };
 
 __device__ __forceinline__ void write_res(const EmbedArgs &e, bool stats)
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
     if (blockIdx.x == 0)
         s1::embed_tail<STATS>(e.a, changed, sse);
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&e.res->changed));
+        block_stats(changed, sse, e.res, e.slot);
 }
 
 // Byte path for buffers that are not 16-byte aligned: one thread per stream
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(512) embed_bytes(EmbedArgs e)
                                  (e.a.n_bytes + 7) >> 3, (uint64_t)gridDim.x * blockDim.x,
                                  changed, sse);
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&e.res->changed));
+        block_stats(changed, sse, e.res, e.slot);
 }
 
 using s1::ExtractArgs;
@@ -100,7 +101,8 @@ int clamp_vec(int v) { return (v == 1 || v == 2 || v == 8) ? v : 4; }
 
 cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uint64_t t_bytes,
                      const uint8_t *msg, uint64_t slen, bool header, uint32_t nbits, bool stats,
-                     stego_result *res, uint64_t res_msg_bytes, const Shape &sh, cudaStream_t s)
+                     stego_result *res, uint64_t res_msg_bytes, const Shape &sh, cudaStream_t s,
+                     StatSlot *slot)
 {
     EmbedArgs e;
     e.a.cover = cover;
@@ -115,11 +117,12 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
     e.a.pad = 0;
     e.res = res;
     e.res_msg_bytes = res_msg_bytes;
+    e.slot = stats ? slot : nullptr;
     const int T = sh.threads;
     void *args[] = {&e};
     if (aligned16(cover) && aligned16(stego) && bulk_stages(sh))
         return s1_embed_bulk(cover, stego, n_bytes, t_bytes, msg, slen, header, nbits, stats,
-                             res, res_msg_bytes, sh, s);
+                             res, res_msg_bytes, sh, s, slot);
     if (aligned16(cover) && aligned16(stego)) {
         const int vec = clamp_vec(sh.vec);
         const void *k = nullptr;

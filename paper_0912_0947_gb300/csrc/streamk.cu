@@ -49,6 +49,7 @@ struct KView {
     uint64_t part_units;  // embed: units touching the stream, ceil(t_bits / 16k)
     uint32_t msg_w4;      // embed: msg - (header bytes) is 4-byte aligned
     uint32_t pad;
+    StatSlot *slot;       // embed: per-stream statistics slot or nullptr
 };
 
 __device__ __forceinline__ uint64_t carry_pos(const KView &a, uint64_t x)
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(512) embedk_units(KView a)
         }
     }
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&a.res->changed));
+        block_stats(changed, sse, a.res, a.slot);
 }
 
 // One thread per carrying byte x < n_carry (all bytes: the bytes past the
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(512) embedk_bytes(KView a)
         }
     }
     if (STATS)
-        block_add2(changed, sse, reinterpret_cast<unsigned long long *>(&a.res->changed));
+        block_stats(changed, sse, a.res, a.slot);
 }
 
 // Stream bit b read back from the stego.
@@ -641,7 +642,8 @@ const void *extract_units_kernel(uint32_t k, uint32_t ch, uint32_t plane)
 
 cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t k, bool plane_only,
                      const stego_geom *g, const uint8_t *msg, uint64_t m, bool header,
-                     bool stats, stego_result *res, const Shape &sh, cudaStream_t s)
+                     bool stats, stego_result *res, const Shape &sh, cudaStream_t s,
+                     StatSlot *slot)
 {
     KView a;
     std::memset(&a, 0, sizeof(a));
@@ -659,6 +661,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     a.plane = plane_only ? g->plane : 0u;
     a.res = res;
     a.res_msg_bytes = m;
+    a.slot = stats ? slot : nullptr;
     a.full_units = a.t_bits / (16u * k);
     a.part_units = (a.t_bits + 16u * k - 1) / (16u * k);
     a.msg_w4 = (((uintptr_t)msg - (header ? 4u : 0u)) & 3u) == 0;
