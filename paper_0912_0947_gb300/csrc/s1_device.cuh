@@ -156,6 +156,106 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
     }
 }
 
+// ---------------------------------------------------------------------------
+// Misaligned buffers
+// ---------------------------------------------------------------------------
+
+// Byte q of the stream, 0 at or past its end.
+__device__ __forceinline__ uint32_t stream_byte_or0(const EmbedView &a, uint64_t q)
+{
+    return q < a.slen ? stream_byte(a, q) : 0u;
+}
+
+// The stream bits of cover bytes k0..k0+15 for any k0, as S[2v] | S[2v+1]
+// << 8 would give them for k0 = 16v: three stream bytes, cut at bit k0 % 8.
+__device__ __forceinline__ uint32_t stream_bits16(const EmbedView &a, uint64_t k0)
+{
+    const uint64_t q = k0 >> 3;
+    const uint32_t w = (stream_byte_or0(a, q) << 16) | (stream_byte_or0(a, q + 1) << 8) |
+                       stream_byte_or0(a, q + 2);
+    const uint32_t bits = (w >> (8u - (uint32_t)(k0 & 7u))) & 0xFFFFu; // byte k0's bit on top
+    return (bits >> 8) | ((bits & 0xFFu) << 8);
+}
+
+// A vector that holds the end of the carrying bytes: bytes from t on keep
+// the cover.
+static __device__ __noinline__ uint4 keep_past_end(uint4 o, const uint4 &c, uint32_t carrying)
+{
+    uint32_t ow[4] = {o.x, o.y, o.z, o.w};
+    const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int n = (int)carrying - 4 * i; // carrying bytes in word i
+        const uint32_t m = n >= 4 ? 0xFFFFFFFFu : (n <= 0 ? 0u : (1u << (8 * n)) - 1u);
+        ow[i] = (ow[i] & m) | (cw[i] & ~m);
+    }
+    return make_uint4(ow[0], ow[1], ow[2], ow[3]);
+}
+
+// Cover bytes k0..k0+15 (any k0, the vector itself 16-byte aligned) with
+// their stream bits p -> stego vector; n += changed bytes when STATS.
+template <bool STATS>
+__device__ __forceinline__ uint4 embed_vec16_at(const EmbedView &a, uint64_t k0, const uint4 &c,
+                                                uint32_t p, uint32_t &n)
+{
+    if (k0 >= a.t_bytes)
+        return c;
+    uint4 o;
+    const uint32_t r0 = __byte_perm(p, 0u, 0x0000u);
+    const uint32_t r1 = __byte_perm(p, 0u, 0x1111u);
+    o.x = (c.x & 0xFEFEFEFEu) | spread_hi(r0);
+    o.y = (c.y & 0xFEFEFEFEu) | spread_lo(r0);
+    o.z = (c.z & 0xFEFEFEFEu) | spread_hi(r1);
+    o.w = (c.w & 0xFEFEFEFEu) | spread_lo(r1);
+    if (k0 + 16 > a.t_bytes)
+        o = keep_past_end(o, c, (uint32_t)(a.t_bytes - k0));
+    if (STATS)
+        n += lsb_changes(o.x, c.x) + lsb_changes(o.y, c.y) + lsb_changes(o.z, c.z) +
+             lsb_changes(o.w, c.w);
+    return o;
+}
+
+// Cover and stego with the same misalignment: h = (-cover) mod 16 head
+// bytes, then aligned vectors j at cover + h + 16j (j < j_end), each with
+// the stream bits of bytes h + 16j onwards.  Head and tail bytes are left to
+// the caller.
+template <int V, bool STATS>
+__device__ __forceinline__ void embed_shift_range(const EmbedView &a, uint32_t h,
+                                                  uint64_t j_first, uint64_t j_end,
+                                                  uint64_t step, unsigned long long &changed,
+                                                  unsigned long long &sse)
+{
+    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover + h);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.stego + h);
+    uint32_t n = 0;
+    for (uint64_t j0 = j_first; j0 < j_end; j0 += step) {
+        uint4 c[V];
+        uint32_t p[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t j = j0 + (uint64_t)u * blockDim.x;
+            if (j < j_end)
+                c[u] = __ldcs(src + j);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t j = j0 + (uint64_t)u * blockDim.x;
+            const uint64_t k0 = h + (j << 4);
+            p[u] = (j < j_end && k0 < a.t_bytes) ? stream_bits16(a, k0) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t j = j0 + (uint64_t)u * blockDim.x;
+            if (j < j_end)
+                __stcs(dst + j, embed_vec16_at<STATS>(a, h + (j << 4), c[u], p[u], n));
+        }
+    }
+    if (STATS) {
+        changed += n;
+        sse += n;
+    }
+}
+
 // One byte k of a job (tails and unaligned buffers).
 template <bool STATS>
 __device__ __forceinline__ void embed_one(const EmbedView &a, uint64_t k, uint32_t s,
@@ -270,6 +370,62 @@ __device__ __forceinline__ void extract_bytes_range(const ExtractView &x, uint64
 {
     for (uint64_t q = q_first; q < q_end; q += step)
         extract_one(x, q);
+}
+
+// The LSBs of 32 bytes (two vectors) as one word, first byte on top.
+__device__ __forceinline__ uint32_t lsb32(const uint4 &lo, const uint4 &hi)
+{
+    return (gather4(lo.x) << 28) | (gather4(lo.y) << 24) | (gather4(lo.z) << 20) |
+           (gather4(lo.w) << 16) | (gather4(hi.x) << 12) | (gather4(hi.y) << 8) |
+           (gather4(hi.z) << 4) | gather4(hi.w);
+}
+
+// A stego whose carrying bytes (st + base) are not 16-byte aligned (a =
+// their address mod 16): message bytes 2v, 2v+1 come from the two aligned
+// vectors around stego bytes base + 16v .. base + 16v + 15, cut at a.  A
+// pair whose two vectors are not both inside the stego goes byte by byte.
+template <int V>
+__device__ __forceinline__ void extract_shift_range(const ExtractView &x, uint64_t C,
+                                                    uint64_t v_first, uint64_t v_end,
+                                                    uint64_t step)
+{
+    const uintptr_t p0 = (uintptr_t)(x.st + x.base);
+    const uint32_t a = (uint32_t)(p0 & 15u);
+    const uint4 *__restrict__ A = reinterpret_cast<const uint4 *>(p0 - a);
+    const uintptr_t lo_ok = (uintptr_t)x.st, hi_ok = (uintptr_t)x.st + C;
+    for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
+        uint4 lo[V], hi[V];
+        bool fast[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            const uintptr_t b = (uintptr_t)(A + v);
+            fast[u] = v < v_end && b >= lo_ok && b + 32u <= hi_ok;
+            if (fast[u]) {
+                lo[u] = __ldcs(A + v);
+                hi[u] = __ldcs(A + v + 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
+            if (v >= v_end)
+                continue;
+            if (!fast[u]) {
+                extract_one(x, 2 * v);
+                extract_one(x, 2 * v + 1);
+                continue;
+            }
+            const uint32_t bits = (lsb32(lo[u], hi[u]) >> (16u - a)) & 0xFFFFu;
+            const uint32_t pair = (bits >> 8) | ((bits & 0xFFu) << 8);
+            if (x.msg_even) {
+                *reinterpret_cast<unsigned short *>(x.msg + 2 * v) = (unsigned short)pair;
+            } else {
+                x.msg[2 * v] = (uint8_t)pair;
+                x.msg[2 * v + 1] = (uint8_t)(pair >> 8);
+            }
+        }
+    }
 }
 
 // Validity of a header value: the count must be whole bytes, fit the stego

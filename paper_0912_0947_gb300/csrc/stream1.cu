@@ -9,6 +9,10 @@
 // (T = carrying bytes).  Each byte is read once and written once, so nothing
 // is staged through shared memory: 128-bit streaming loads/stores with V
 // vectors in flight per thread over a persistent grid feed HBM directly.
+// Misaligned buffers: cover and stego with the same address mod 16 run
+// aligned vectors after a head of scalar bytes (the stream cut at the head's
+// bit offset); a misaligned stego is read as aligned vector pairs; only an
+// embed whose cover and stego differ mod 16 runs byte by byte.
 #include "s1_device.cuh"
 
 namespace stego {
@@ -52,8 +56,32 @@ __global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
         block_stats(changed, sse, e.res, e.slot);
 }
 
-// Byte path for buffers that are not 16-byte aligned: one thread per stream
-// byte (eight cover bytes).
+// Cover and stego with the same misalignment: aligned vectors after h head
+// bytes, the stream cut at bit h % 8; block 0 does the head and the tail
+// (fewer than 32 bytes).  Requires n_bytes >= h.
+template <int V, bool STATS>
+__global__ void __launch_bounds__(512) embed_shift(EmbedArgs e, uint32_t h)
+{
+    unsigned long long changed = 0, sse = 0;
+    write_res(e, STATS);
+    const uint64_t nvb = (e.a.n_bytes - h) >> 4;
+    s1::embed_shift_range<V, STATS>(e.a, h, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x,
+                                    nvb, (uint64_t)gridDim.x * blockDim.x * V, changed, sse);
+    if (blockIdx.x == 0) {
+        const uint32_t tail = (uint32_t)(e.a.n_bytes - h - (nvb << 4));
+        if (threadIdx.x < h + tail) {
+            const uint64_t k = threadIdx.x < h ? (uint64_t)threadIdx.x
+                                               : h + (nvb << 4) + (threadIdx.x - h);
+            const uint32_t sb = k < e.a.t_bytes ? s1::stream_byte(e.a, k >> 3) : 0u;
+            s1::embed_one<STATS>(e.a, k, sb, changed, sse);
+        }
+    }
+    if (STATS)
+        block_stats(changed, sse, e.res, e.slot);
+}
+
+// Byte path for cover and stego with different misalignments: one thread
+// per stream byte (eight cover bytes).
 template <bool STATS>
 __global__ void __launch_bounds__(512) embed_bytes(EmbedArgs e)
 {
@@ -82,18 +110,25 @@ __global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
         s1::extract_one(x, x.len - 1);
 }
 
-// Byte path for a stego that is not 16-byte aligned: one thread per message
-// byte.
-__global__ void __launch_bounds__(512) extract_bytes(ExtractArgs a)
+// A stego that is not 16-byte aligned: each message byte pair from the two
+// aligned vectors around its 16 stego bytes.
+template <int V>
+__global__ void __launch_bounds__(512) extract_shift(ExtractArgs a)
 {
     ExtractView x;
     if (extract_prologue(a, x) != STEGO_OK)
         return;
-    s1::extract_bytes_range(x, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, x.len,
-                            (uint64_t)gridDim.x * blockDim.x);
+    s1::extract_shift_range<V>(x, a.C, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x,
+                               x.len >> 1, (uint64_t)gridDim.x * blockDim.x * V);
+    if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0)
+        s1::extract_one(x, x.len - 1);
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Vectors in flight per thread in the misaligned kernels (their stream
+// windows and vector pairs take more registers than the aligned ones).
+constexpr int kShiftV = 1;
 
 int clamp_vec(int v) { return (v == 1 || v == 2 || v == 8) ? v : 4; }
 
@@ -136,6 +171,15 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
         const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvec > 0 ? nvec : 1,
                                          (uint64_t)T * vec);
         return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    }
+    const uint32_t h = (uint32_t)((16u - ((uintptr_t)cover & 15u)) & 15u);
+    if ((((uintptr_t)cover ^ (uintptr_t)stego) & 15u) == 0 && n_bytes >= (uint64_t)h + 16u) {
+        const void *k = stats ? (const void *)embed_shift<kShiftV, true>
+                              : (const void *)embed_shift<kShiftV, false>;
+        const uint64_t nvb = (n_bytes - h) >> 4;
+        const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvb, (uint64_t)T * kShiftV);
+        void *sargs[] = {&e, (void *)&h};
+        return cudaLaunchKernel(k, dim3(grid), dim3(T), sargs, 0, s);
     }
     const void *k = stats ? (const void *)embed_bytes<true> : (const void *)embed_bytes<false>;
     const uint64_t units = (n_bytes + 7) >> 3;
@@ -180,9 +224,10 @@ cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap
                                          (uint64_t)T * vec);
         return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
     }
-    const void *k = (const void *)extract_bytes;
-    const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, max_len > 0 ? max_len : 1,
-                                     (uint64_t)T);
+    const void *k = (const void *)extract_shift<kShiftV>;
+    const uint64_t npairs = max_len >> 1;
+    const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, npairs > 0 ? npairs : 1,
+                                     (uint64_t)T * kShiftV);
     return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
 }
 

@@ -258,3 +258,45 @@ def test_single_8192_full_capacity(S, O):
     buf = cover.clone()
     S.stego_embed(buf, buf, msg, S.HEADER_BE32)
     assert torch.equal(buf, stego)
+
+
+@pytest.mark.parametrize("off", range(1, 16))
+def test_same_misalignment_vector_path(S, O, off):
+    """Cover and stego at the same address mod 16 (the head-then-vectors
+    path, the stream cut at every bit offset) and a misaligned stego for the
+    extraction (aligned vector pairs), header and raw, in and out of place."""
+    rng = np.random.default_rng(700 + off)
+    C = 3 * 4096 + 77
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    for header in (True, False):
+        cap = S.stego_capacity(C, S.HEADER_BE32 if header else 0)
+        for m in sorted({0, 1, 2, 37, cap // 2 + 1, cap}):
+            msg = rng.integers(0, 256, m, dtype=np.uint8)
+            stego = _embed_check(S, O, cover, msg, header, offs=(off, off, off % 3))
+            _embed_check(S, O, cover, msg, header, offs=(off, off, 0), inplace=True)
+            if stego is not None:
+                _extract_check(S, O, stego, m, header, offs=(off, (off * 5) % 16))
+
+
+def test_same_misalignment_full_size(S, O):
+    """The 8192x8192x3 cover at full capacity, cover and stego both 3 bytes
+    past a 16-byte boundary, and the extraction from that stego."""
+    w = synth.single_8192()
+    C, m = w.cover_bytes, w.msg_bytes
+    cbuf = torch.empty(C + 16, dtype=torch.uint8, device="cuda")
+    sbuf = torch.empty(C + 16, dtype=torch.uint8, device="cuda")
+    cover = cbuf[3:3 + C]
+    cover.copy_(w.cover("cuda"))
+    stego = sbuf[3:3 + C]
+    msg = w.message("cuda")
+    res = S.new_result()
+    S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res)
+    out = torch.empty(m, dtype=torch.uint8, device="cuda")
+    res2 = S.new_result()
+    S.stego_extract(stego, out, 0, S.HEADER_BE32, res2)
+    c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+    st, want = O.stream1_embed(c_h, m_h, header=True)
+    assert st == 0 and np.array_equal(stego.cpu().numpy(), want)
+    r = S.read_result(res)
+    assert (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+    assert S.read_result(res2)["msg_bytes"] == m and torch.equal(out, msg)
