@@ -60,7 +60,8 @@ static_assert(sizeof(DescInfo) == 64, "DescInfo is 64 bytes");
 
 constexpr uint32_t kHeader = 1u, kVec = 2u, kMsgEven = 4u;
 // paper-layout work kinds (0 = the one-bit stream layout)
-constexpr uint32_t kP2Units = 1u, kP2RowsCopy = 2u, kP2Rows = 3u, kP2Runs = 4u, kP2RowsX = 5u;
+constexpr uint32_t kP2Units = 1u, kP2RowsCopy = 2u, kP2Rows = 3u, kP2Runs = 4u, kP2RowsX = 5u,
+                   kP2UnitsInPlace = 6u;
 constexpr uint32_t kChunk = 4u; // tiles per claim
 
 // Workspace: head (64 B), stream tile offsets (n+1), paper tile offsets
@@ -189,6 +190,15 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
                 const uint64_t units = (uint64_t)(D.geom.width / 16u) * D.geom.height;
                 const uint64_t per = tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u;
                 inf.mode = kP2Units;
+                inf.per_tile = (uint32_t)per;
+                tiles = (units + per - 1) / per;
+            } else if (inplace && d_aligned16(D.cover) && (ch == 3 || ch == 1) &&
+                       D.geom.plane == 0 && D.geom.width % 16u == 0 &&
+                       (uint64_t)D.geom.width / 16u * D.geom.height < (1ull << 31)) {
+                // in place: the units of the carrying rows, written back whole
+                const uint64_t units = (uint64_t)(D.geom.width / 16u) * v.R;
+                const uint64_t per = tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u;
+                inf.mode = kP2UnitsInPlace;
                 inf.per_tile = (uint32_t)per;
                 tiles = (units + per - 1) / per;
             } else if (!inplace) {
@@ -440,8 +450,13 @@ __device__ __forceinline__ void paper_embed_tile(const stego_desc &D, const Desc
     const p2::View v = p2::make_view(D.cover, D.stego, inf.W, inf.H, inf.channels, inf.plane,
                                      D.msg, nullptr, inf.len);
     const uint64_t b0 = lt * inf.per_tile, b1 = b0 + inf.per_tile;
-    if (inf.mode == kP2Units) {
-        const uint64_t units = (uint64_t)(inf.W / 16u) * inf.H;
+    if (inf.mode == kP2Units || inf.mode == kP2UnitsInPlace) {
+        // in place the same code runs over the carrying rows' units only:
+        // each unit is read and written back by one thread, so src == dst is
+        // safe, and the last row's units past its carrying columns are
+        // rewritten unchanged (one instantiation keeps the registers down)
+        const bool ip = inf.mode == kP2UnitsInPlace;
+        const uint64_t units = (uint64_t)(inf.W / 16u) * (ip ? v.R : inf.H);
         const uint32_t k0 = (uint32_t)b0 + threadIdx.x;
         const uint32_t k1 = (uint32_t)(b1 < units ? b1 : units);
         if (inf.channels == 3)

@@ -160,11 +160,14 @@ __device__ __forceinline__ void pair_stats(const uint4 &o, const uint4 &c,
     sse += s;
 }
 
-// Out of place, one pass over units k = k_first + i*step (+ u*blockDim.x,
-// u < UT), k < k_end, of an image whose rows are whole units and whose
-// buffers are 16-byte aligned.  Each thread issues the cover loads of its UT
-// units, then their message loads, before any arithmetic.
-template <int CH, int PLANE, bool STATS, int UT>
+// One pass over units k = k_first + i*step (+ u*blockDim.x, u < UT),
+// k < k_end, of an image whose rows are whole units and whose buffers are
+// 16-byte aligned.  Out of place every unit is written (units without
+// carrying pixels are copied) and each thread issues the cover loads of its
+// UT units, then their message loads, before any arithmetic.  In place
+// (INPLACE, k_end at most the units of the carrying rows) only units with
+// carrying pixels are read and written back whole.
+template <int CH, int PLANE, bool STATS, int UT, bool INPLACE = false>
 __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uint32_t k_end,
                                             uint32_t step, unsigned long long &changed,
                                             unsigned long long &sse)
@@ -175,13 +178,15 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
     uint4 *dst = reinterpret_cast<uint4 *>(a.dst);
     for (uint32_t k0 = k_first; k0 < k_end; k0 += step) {
         uint4 c[UT][CH];
+        if constexpr (!INPLACE) {
 #pragma unroll
-        for (int u = 0; u < UT; ++u) {
-            const uint32_t k = k0 + u * blockDim.x;
-            if (k < k_end) {
+            for (int u = 0; u < UT; ++u) {
+                const uint32_t k = k0 + u * blockDim.x;
+                if (k < k_end) {
 #pragma unroll
-                for (int q = 0; q < CH; ++q)
-                    c[u][q] = __ldcs(src + (uint64_t)k * CH + q);
+                    for (int q = 0; q < CH; ++q)
+                        c[u][q] = __ldcs(src + (uint64_t)k * CH + q);
+                }
             }
         }
         int mode[UT]; // 0: copy only, 1: one quarter (SWAR), 2: per pixel
@@ -207,10 +212,21 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
                 }
             }
         }
+        if constexpr (INPLACE) {
+#pragma unroll
+            for (int u = 0; u < UT; ++u) {
+                if (mode[u]) {
+                    const uint32_t k = k0 + u * blockDim.x;
+#pragma unroll
+                    for (int q = 0; q < CH; ++q)
+                        c[u][q] = __ldcs(src + (uint64_t)k * CH + q);
+                }
+            }
+        }
 #pragma unroll
         for (int u = 0; u < UT; ++u) {
             const uint32_t k = k0 + u * blockDim.x;
-            if (k >= k_end)
+            if (k >= k_end || (INPLACE && !mode[u]))
                 continue;
             uint4 o[CH];
 #pragma unroll

@@ -3,9 +3,11 @@
 // among rows, pair i of B[j] at A[L*i + j]).  The per-unit, per-run and
 // per-row routines live in p2_device.cuh and are shared with the batched
 // kernels.
-//   p2_embed_units<CH,PLANE>  out of place, one pass (2C + N bytes),
-//       persistent grid over 16-pixel units; 256-thread CTAs, 3 per SM.
-//   p2_embed_rows  in place, and the scatter after a copy for layouts the
+//   p2_embed_units<CH,PLANE,STATS,INPLACE>  persistent grid over 16-pixel
+//       units; 256-thread CTAs, 3 per SM.  Out of place one pass (2C + N
+//       bytes); in place the units of the carrying rows, read and written
+//       back whole.
+//   p2_embed_rows  the scatter after a copy (and in place) for layouts the
 //       unit kernel does not take; CTAs stride over carrying rows.
 //   p2_extract_units<CH,PLANE>  runs of 16 message bytes (CH in {1,3,4}).
 //   p2_extract_rows  any channel count.
@@ -38,13 +40,15 @@ __device__ __forceinline__ void write_res(const P2Args &a, bool stats)
 constexpr int kUnitThreads = 256; // p2_embed_units' register bound assumes it
 constexpr int kUnitsPerThread = 2;
 
-template <int CH, int PLANE, bool STATS>
+// Out of place every unit of the image; in place the units of the carrying
+// rows (those without carrying pixels are skipped).
+template <int CH, int PLANE, bool STATS, bool INPLACE>
 __global__ void __launch_bounds__(kUnitThreads, 3) p2_embed_units(P2Args a)
 {
     unsigned long long changed = 0, sse = 0;
     write_res(a, STATS);
-    const uint32_t nunits = a.v.W / 16 * a.v.H;
-    p2::units_embed<CH, PLANE, STATS, kUnitsPerThread>(
+    const uint32_t nunits = a.v.W / 16 * (INPLACE ? a.v.R : a.v.H);
+    p2::units_embed<CH, PLANE, STATS, kUnitsPerThread, INPLACE>(
         a.v, blockIdx.x * blockDim.x * kUnitsPerThread + threadIdx.x, nunits,
         gridDim.x * blockDim.x * kUnitsPerThread, changed, sse);
     if (STATS)
@@ -102,24 +106,33 @@ int row_grid(const void *k, const Shape &sh, uint32_t rows)
     return persistent_grid(k, sh.threads, 0, sh.ctas_per_sm, rows ? rows : 1, 1);
 }
 
-template <bool STATS>
+template <bool STATS, bool INPLACE>
 const void *units_kernel(uint32_t ch, uint32_t plane)
 {
     if (ch == 1)
-        return (const void *)p2_embed_units<1, 0, STATS>;
+        return (const void *)p2_embed_units<1, 0, STATS, INPLACE>;
     if (ch == 3) {
         switch (plane) {
-        case 0: return (const void *)p2_embed_units<3, 0, STATS>;
-        case 1: return (const void *)p2_embed_units<3, 1, STATS>;
-        default: return (const void *)p2_embed_units<3, 2, STATS>;
+        case 0: return (const void *)p2_embed_units<3, 0, STATS, INPLACE>;
+        case 1: return (const void *)p2_embed_units<3, 1, STATS, INPLACE>;
+        default: return (const void *)p2_embed_units<3, 2, STATS, INPLACE>;
         }
     }
     switch (plane) {
-    case 0: return (const void *)p2_embed_units<4, 0, STATS>;
-    case 1: return (const void *)p2_embed_units<4, 1, STATS>;
-    case 2: return (const void *)p2_embed_units<4, 2, STATS>;
-    default: return (const void *)p2_embed_units<4, 3, STATS>;
+    case 0: return (const void *)p2_embed_units<4, 0, STATS, INPLACE>;
+    case 1: return (const void *)p2_embed_units<4, 1, STATS, INPLACE>;
+    case 2: return (const void *)p2_embed_units<4, 2, STATS, INPLACE>;
+    default: return (const void *)p2_embed_units<4, 3, STATS, INPLACE>;
     }
+}
+
+// Units need 1, 3 or 4 channels, rows of whole 16-byte vectors and a
+// 16-byte aligned buffer; unit indices are counted in 32 bits (plus a grid
+// stride of headroom).
+bool units_layout_ok(const uint8_t *buf, const stego_geom &g)
+{
+    return (((uintptr_t)buf & 15u) == 0) && p2::unit_channels(g.channels) &&
+           g.width % 16u == 0 && (uint64_t)g.width / 16u * g.height < (1ull << 31);
 }
 
 const void *extract_units_kernel(uint32_t ch, uint32_t plane)
@@ -145,10 +158,7 @@ const void *extract_units_kernel(uint32_t ch, uint32_t plane)
 
 bool p2_fused_ok(const uint8_t *cover, const uint8_t *stego, const stego_geom &g)
 {
-    // units of 16 pixels are counted in 32 bits (plus a grid stride of headroom)
-    return cover != stego && ((((uintptr_t)cover | (uintptr_t)stego) & 15u) == 0) &&
-           p2::unit_channels(g.channels) && g.width % 16u == 0 &&
-           (uint64_t)g.width / 16u * g.height < (1ull << 31);
+    return cover != stego && units_layout_ok(cover, g) && units_layout_ok(stego, g);
 }
 
 cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
@@ -157,8 +167,8 @@ cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geo
 {
     P2Args a = make_args(cover, stego, g, msg, nullptr, N, res);
     a.slot = stats ? slot : nullptr;
-    const void *k = stats ? units_kernel<true>(g.channels, g.plane)
-                          : units_kernel<false>(g.channels, g.plane);
+    const void *k = stats ? units_kernel<true, false>(g.channels, g.plane)
+                          : units_kernel<false, false>(g.channels, g.plane);
     const uint64_t nunits = (uint64_t)(g.width / 16u) * g.height;
     const int grid = persistent_grid(k, kUnitThreads, 0, sh.ctas_per_sm, nunits ? nunits : 1,
                                      (uint64_t)kUnitThreads * kUnitsPerThread);
@@ -172,6 +182,18 @@ cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
 {
     P2Args a = make_args(cover, stego, g, msg, nullptr, N, res);
     a.slot = stats ? slot : nullptr;
+    if (cover == stego && units_layout_ok(stego, g)) {
+        // in place over the units of the carrying rows: whole vectors
+        // instead of one byte access per plane byte
+        const void *k = stats ? units_kernel<true, true>(g.channels, g.plane)
+                              : units_kernel<false, true>(g.channels, g.plane);
+        const uint64_t nunits = (uint64_t)(g.width / 16u) * a.v.R;
+        const int grid = persistent_grid(k, kUnitThreads, 0, sh.ctas_per_sm,
+                                         nunits ? nunits : 1,
+                                         (uint64_t)kUnitThreads * kUnitsPerThread);
+        void *args[] = {&a};
+        return cudaLaunchKernel(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
+    }
     const void *k = stats ? (const void *)p2_embed_rows<true> : (const void *)p2_embed_rows<false>;
     const int grid = row_grid(k, sh, a.v.R);
     void *args[] = {&a};
