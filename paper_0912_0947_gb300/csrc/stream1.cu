@@ -41,15 +41,24 @@ __device__ __forceinline__ void write_res(const EmbedArgs &e, bool stats)
     }
 }
 
-// Vector path (cover and stego 16-byte aligned), persistent grid.
+// Vector path (cover and stego 16-byte aligned), persistent grid.  Whole
+// rounds of V vectors per thread cover the vectors up to the last multiple
+// of the grid's round; the remainder is spread one vector per thread over
+// the whole grid, so every CTA ends within a fraction of a round of the
+// others (with rounds dealt whole, a quarter of the CTAs would run one round
+// longer on the 201 MB cover).
 template <int V, bool STATS>
 __global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
 {
     unsigned long long changed = 0, sse = 0;
     write_res(e, STATS);
+    const uint64_t nvec = e.a.n_bytes >> 4;
+    const uint64_t round = (uint64_t)gridDim.x * blockDim.x * V;
+    const uint64_t whole = nvec / round * round;
     s1::embed_vec_range<V, STATS>(e.a, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x,
-                                  e.a.n_bytes >> 4, (uint64_t)gridDim.x * blockDim.x * V,
-                                  changed, sse);
+                                  whole, round, changed, sse);
+    s1::embed_vec_range<1, STATS>(e.a, whole + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                  nvec, (uint64_t)gridDim.x * blockDim.x, changed, sse);
     if (blockIdx.x == 0)
         s1::embed_tail<STATS>(e.a, changed, sse);
     if (STATS)
@@ -104,8 +113,12 @@ __global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
     ExtractView x;
     if (extract_prologue(a, x) != STEGO_OK)
         return;
-    s1::extract_vec_range<V>(x, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x, x.len >> 1,
-                             (uint64_t)gridDim.x * blockDim.x * V);
+    const uint64_t nvec = x.len >> 1;
+    const uint64_t round = (uint64_t)gridDim.x * blockDim.x * V;
+    const uint64_t whole = nvec / round * round; // the remainder spread as in embed_vec
+    s1::extract_vec_range<V>(x, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x, whole, round);
+    s1::extract_vec_range<1>(x, whole + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nvec,
+                             (uint64_t)gridDim.x * blockDim.x);
     if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0)
         s1::extract_one(x, x.len - 1);
 }
