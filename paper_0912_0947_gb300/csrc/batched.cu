@@ -560,8 +560,8 @@ __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, 
 // The paper layout's own persistent kernels (a separate register budget from
 // the stream kernels): tiles of units, rows or runs, claimed like above.
 // Capped at 80 registers for three CTAs per SM: on 600 video frames the
-// embed went from 1.47 to 1.32 ms and the extract from 0.54 to 0.48 ms (the
-// statistics variant spills 92 bytes, off the unit loop's hot path).
+// embed with statistics went from 1.47 to 1.32 ms and the extract from 0.54
+// to 0.48 ms, although the statistics variant now spills 92 bytes.
 template <bool STATS>
 __global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *descs, uint32_t n,
                                                         stego_result *results, WsView ws)
