@@ -48,7 +48,7 @@ struct KView {
     uint64_t full_units;  // embed: units wholly inside the stream, t_bits / 16k
     uint64_t part_units;  // embed: units touching the stream, ceil(t_bits / 16k)
     uint32_t msg_w4;      // embed: msg - (header bytes) is 4-byte aligned
-    uint32_t pad;
+    uint32_t msg_w2;      // embed: msg - (header bytes) is 2-byte aligned
     StatSlot *slot;       // embed: per-stream statistics slot or nullptr
 };
 
@@ -155,12 +155,19 @@ __device__ __forceinline__ uint64_t stream_window(const KView &a, uint64_t v)
     const uint64_t q0 = 2u * K * v;
     const uint64_t hb = a.header ? 4u : 0u;
     const uint8_t *mp = a.msg + (q0 - hb);
-    // q0 is a multiple of 4 for even K, so mp's alignment is the launch's
+    // q0 is a multiple of 4 for even K (of 2 for K = 3), so mp's alignment
+    // is the launch's
     if ((K & 1) == 0 && q0 >= hb && a.msg_w4) {
 #pragma unroll
         for (int i = 0; i < K / 2; ++i) {
             const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(mp) + i);
             X |= (uint64_t)__byte_perm(w, 0u, 0x0123u) << (32 - 32 * i);
+        }
+    } else if (K == 3 && q0 >= hb && a.msg_w2) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const uint32_t h = __ldg(reinterpret_cast<const unsigned short *>(mp) + i);
+            X |= (uint64_t)__byte_perm(h, 0u, 0x4401u) << (48 - 16 * i); // bytes swapped
         }
     } else {
 #pragma unroll
@@ -263,6 +270,11 @@ __device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
         // stream bytes 2i, 2i+1; lanes take high nibble, low nibble, high, low
         const uint32_t r = __byte_perm(i < 2 ? hi : lo, 0u, (i & 1) ? 0x0011u : 0x2233u);
         return ((r >> 4) & 0x000F000Fu) | (r & 0x0F000F00u);
+    } else if constexpr (K == 3) {
+        // the word's 12 bits, then one 3-bit field per lane
+        const uint32_t t = (uint32_t)(X >> (52 - 12 * i)) & 0xFFFu;
+        return ((t >> 9) & 7u) | (((t >> 6) & 7u) << 8) | (((t >> 3) & 7u) << 16) |
+               ((t & 7u) << 24);
     } else {
         constexpr uint32_t MASK = (1u << K) - 1u;
         uint32_t f = 0;
@@ -301,6 +313,17 @@ __device__ __forceinline__ uint64_t unit_window(const uint32_t (&g)[4])
         const uint32_t hi = __byte_perm(b[0], b[1], 0x0246u); // b0.l0 b0.l2 b1.l0 b1.l2, first on top
         const uint32_t lo = __byte_perm(b[2], b[3], 0x0246u);
         return ((uint64_t)hi << 32) | lo;
+    } else if constexpr (K == 3) {
+        // 12 bits per word, the four words' bits placed from the top
+        uint64_t X = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t w = g[i];
+            const uint32_t t = ((w & 7u) << 9) | (((w >> 8) & 7u) << 6) |
+                               (((w >> 16) & 7u) << 3) | ((w >> 24) & 7u);
+            X |= (uint64_t)t << (52 - 12 * i);
+        }
+        return X;
     } else {
         constexpr uint32_t MASK = (1u << K) - 1u;
         uint64_t X = 0;
@@ -529,6 +552,12 @@ __global__ void __launch_bounds__(512) extractk_units(KView a)
                 for (int i = 0; i < K / 2; ++i)
                     reinterpret_cast<uint32_t *>(op)[i] =
                         __byte_perm((uint32_t)(X >> (32 - 32 * i)), 0u, 0x0123u);
+            } else if (K == 3 && q0 >= hb && q0 + 6 <= sbytes && (((uintptr_t)op & 1u) == 0)) {
+                // three 16-bit stores (2-byte aligned message bytes)
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    reinterpret_cast<unsigned short *>(op)[i] = (unsigned short)__byte_perm(
+                        (uint32_t)(X >> (48 - 16 * i)) & 0xFFFFu, 0u, 0x4401u);
             } else {
 #pragma unroll
                 for (int i = 0; i < 2 * K; ++i) {
@@ -665,6 +694,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     a.full_units = a.t_bits / (16u * k);
     a.part_units = (a.t_bits + 16u * k - 1) / (16u * k);
     a.msg_w4 = (((uintptr_t)msg - (header ? 4u : 0u)) & 3u) == 0;
+    a.msg_w2 = (((uintptr_t)msg - (header ? 4u : 0u)) & 1u) == 0;
     const bool inplace = cover == stego;
     const uint64_t t_carry = (a.t_bits + k - 1) / k; // carrying bytes the stream uses
     const int T = sh.threads;
