@@ -286,7 +286,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if rank == 0 and "serving" in want:
         legs["serving"] = run_serving_leg(S, AT, torch, dev, synth,
-                                          [1000, 2000, 5000, 10000, 20000, 50000])
+                                          [1000, 2000, 5000, 10000, 20000, 50000],
+                                          max_requests=args.serving_max_requests,
+                                          seconds=args.serving_seconds)
         torch.cuda.empty_cache()
     # ---- CPU oracle baseline ----------------------------------------------------
     cpu = None
@@ -621,6 +623,7 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds
         assert torch.equal(out_msg[moff[i]:moff[i] + mlens[i]], msgs[moff[i]:moff[i] + mlens[i]])
     return {"workload": "Poisson open loop, 70% embed / 30% extract, 4096 resident uneven "
                         "covers and stegos, 40 GB in-flight budget, 8 slots, batches <= 512",
+            "per_rate": "max(500, min(%d, rate x %g s)) requests" % (max_requests, seconds),
             "rates": results, "batches": stats["batches"],
             "peak_in_flight_bytes": stats["peak_in_flight_bytes"]}
 
@@ -874,6 +877,29 @@ def oracle_round_trip(O, cover, msg):
     return dt
 
 
+def host_cpu() -> str:
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo) and core count."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return "%s, %d cores" % (name or "unknown CPU", os.cpu_count() or 0)
+
+
 def run_cpu_baseline(cover, msg, budget_s=12.0):
     import oracle
     O = oracle.load()
@@ -882,7 +908,7 @@ def run_cpu_baseline(cover, msg, budget_s=12.0):
         elapsed += oracle_round_trip(O, cover, msg)
         reps += 1
     return {"value": round(2.0 * cover.size * reps / elapsed / 1e9, 4), "unit": UNIT,
-            "cores": 1, "kind": "oracle",
+            "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": "%d embed+extract round trips of the whole %d-byte cover "
                       "(single-threaded C oracle, %.1f s)" % (reps, cover.size, elapsed)}
 
@@ -971,6 +997,10 @@ def main():
                     help="fixed launch shape threads,vec,ctas_per_sm,tile_bytes for the embed "
                          "(tile_bytes > 0: shared-memory staged kernel with that ring)")
     ap.add_argument("--shape-extract", default="", help="same for the extract")
+    ap.add_argument("--serving-seconds", type=float, default=1.0,
+                    help="arrival span per rate of the serving leg (20 for 20 s per rate)")
+    ap.add_argument("--serving-max-requests", type=int, default=20000,
+                    help="request cap per rate of the serving leg")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--uneven-count", type=int, default=0,
