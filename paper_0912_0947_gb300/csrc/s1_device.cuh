@@ -78,12 +78,16 @@ __device__ __forceinline__ uint32_t spread_lo(uint32_t rep)
     return (((rep & 0x01020408u) + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
 }
 
-// Changed bytes of one embedded word.  Only bit 0 of a byte can differ
-// between cover and stego in this layout, so (stego ^ cover) has at most the
-// four bits 0, 8, 16, 24 set and its population count is the number of
-// changed bytes.  Each changed byte moves by exactly one, so the same count
-// is also the word's squared error.
-__device__ __forceinline__ uint32_t lsb_changes(uint32_t o, uint32_t c) { return __popc(o ^ c); }
+// Changed bytes of one embedded vector.  Only bit 0 of a byte can differ
+// between cover and stego in this layout, so each word of (stego ^ cover)
+// has at most the four bits 0, 8, 16, 24 set; the four words shifted by 0..3
+// bits never overlap, and one population count of their OR is the number
+// of changed bytes.  Each changed byte moves by exactly one, so the same
+// count is also the vector's squared error.
+__device__ __forceinline__ uint32_t vec_changes(const uint4 &o, const uint4 &c)
+{
+    return __popc((o.x ^ c.x) | ((o.y ^ c.y) << 1) | ((o.z ^ c.z) << 2) | ((o.w ^ c.w) << 3));
+}
 
 // Cover vector v (bytes 16v..16v+15) with its stream bytes p = S[2v] |
 // S[2v+1] << 8 -> stego vector; n += changed bytes when STATS.
@@ -97,15 +101,13 @@ __device__ __forceinline__ uint4 embed_vec16(const EmbedView &a, uint64_t v, con
         const uint32_t r0 = __byte_perm(p, 0u, 0x0000u);
         o.x = (c.x & 0xFEFEFEFEu) | spread_hi(r0);
         o.y = (c.y & 0xFEFEFEFEu) | spread_lo(r0);
-        if (STATS)
-            n += lsb_changes(o.x, c.x) + lsb_changes(o.y, c.y);
         if (k0 + 8 < a.t_bytes) { // T is a multiple of 8
             const uint32_t r1 = __byte_perm(p, 0u, 0x1111u);
             o.z = (c.z & 0xFEFEFEFEu) | spread_hi(r1);
             o.w = (c.w & 0xFEFEFEFEu) | spread_lo(r1);
-            if (STATS)
-                n += lsb_changes(o.z, c.z) + lsb_changes(o.w, c.w);
         }
+        if (STATS)
+            n += vec_changes(o, c);
     }
     return o;
 }
@@ -113,7 +115,7 @@ __device__ __forceinline__ uint4 embed_vec16(const EmbedView &a, uint64_t v, con
 // 16-byte vectors v = v_first + i*step (+ u*blockDim.x for u < V), v < v_end,
 // of a job whose cover and stego are 16-byte aligned.  Each warp's 128-bit
 // load and store instructions cover 512 contiguous bytes.  With STATS the
-// changed-byte count (= squared error, see lsb_changes) is added to both
+// changed-byte count (= squared error, see vec_changes) is added to both
 // accumulators.
 template <int V, bool STATS>
 __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_first,
@@ -126,9 +128,39 @@ __device__ __forceinline__ void embed_vec_range(const EmbedView &a, uint64_t v_f
     // changed bytes of this call in 32 bits: a thread covers at most
     // (bytes / threads) bytes, far below 2^32 for any cover in device memory
     uint32_t n = 0;
+    // vectors [fast_lo, fast_hi) carry message bytes only (two per vector, a
+    // 16-bit load when the message is 2-byte aligned) in all 16 bytes
+    const uint64_t fast_lo = a.header ? 2u : 0u;
+    const uint64_t fast_hi = a.msg_even ? (a.t_bytes >> 4) : 0u;
+    const unsigned short *__restrict__ mw =
+        reinterpret_cast<const unsigned short *>(a.msg) - fast_lo;
     for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
         uint4 c[V];
         uint32_t p[V];
+        const uint64_t vlast = v0 + (uint64_t)(V - 1) * blockDim.x;
+        if (v0 >= fast_lo && vlast < fast_hi && vlast < v_end) {
+            // the whole round inside the message: no per-vector checks
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                c[u] = __ldcs(src + v0 + (uint64_t)u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                p[u] = __ldg(mw + v0 + (uint64_t)u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                const uint32_t r0 = __byte_perm(p[u], 0u, 0x0000u);
+                const uint32_t r1 = __byte_perm(p[u], 0u, 0x1111u);
+                uint4 o;
+                o.x = (c[u].x & 0xFEFEFEFEu) | spread_hi(r0);
+                o.y = (c[u].y & 0xFEFEFEFEu) | spread_lo(r0);
+                o.z = (c[u].z & 0xFEFEFEFEu) | spread_hi(r1);
+                o.w = (c[u].w & 0xFEFEFEFEu) | spread_lo(r1);
+                if (STATS)
+                    n += vec_changes(o, c[u]);
+                __stcs(dst + v0 + (uint64_t)u * blockDim.x, o);
+            }
+            continue;
+        }
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const uint64_t v = v0 + (uint64_t)u * blockDim.x;
@@ -210,8 +242,7 @@ __device__ __forceinline__ uint4 embed_vec16_at(const EmbedView &a, uint64_t k0,
     if (k0 + 16 > a.t_bytes)
         o = keep_past_end(o, c, (uint32_t)(a.t_bytes - k0));
     if (STATS)
-        n += lsb_changes(o.x, c.x) + lsb_changes(o.y, c.y) + lsb_changes(o.z, c.z) +
-             lsb_changes(o.w, c.w);
+        n += vec_changes(o, c);
     return o;
 }
 
@@ -330,8 +361,19 @@ __device__ __forceinline__ void extract_vec_range(const ExtractView &x, uint64_t
                                                   uint64_t v_end, uint64_t step)
 {
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(x.st + x.base);
+    unsigned short *mw = reinterpret_cast<unsigned short *>(x.msg);
     for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
         uint4 c[V];
+        if (x.msg_even && v0 + (uint64_t)(V - 1) * blockDim.x < v_end) {
+            // a whole round: no per-vector checks, 16-bit message stores
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                c[u] = __ldcs(src + v0 + (uint64_t)u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                mw[v0 + (uint64_t)u * blockDim.x] = (unsigned short)gather16(c[u]);
+            continue;
+        }
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const uint64_t v = v0 + (uint64_t)u * blockDim.x;
