@@ -39,8 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_write.sum) from one ncu capture on this exact workload, per
 # kernel family, valid only while the kernel sources hash to `src_sha`.
 # Writes still dirty in the L2 when the kernel exits are not in the count.
-NCU_TRAFFIC = {"embed_vec": {"src_sha": "caa3e43db2b6c22f", "bytes": 226523648 + 143607040},
-               "embed_bulk": {"src_sha": "caa3e43db2b6c22f", "bytes": 226561280 + 142696448}}
+NCU_TRAFFIC = {"embed_vec": {"src_sha": "c5b02751867fd4e8", "bytes": 226526464 + 145063680},
+               "embed_bulk": {"src_sha": "c5b02751867fd4e8", "bytes": 226599680 + 142849024}}
 KERNEL_SOURCES = ("s1_device.cuh", "stream1.cu", "bulk.cu", "internal.cuh")
 MAX_RING = 192 * 1024
 
