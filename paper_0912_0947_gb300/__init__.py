@@ -190,7 +190,7 @@ def _dev_ptr(t, what: str, dtype=torch.uint8):
         return None
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch.Tensor" % what)
-    if t.device.type != "cuda":
+    if not t.is_cuda:  # (a bool property: cheaper than building t.device)
         if not (t.device.type == "cpu" and t.is_pinned()):
             raise ValueError("%s must live on a CUDA device or in pinned host memory "
                              "(no CPU fallback)" % what)
