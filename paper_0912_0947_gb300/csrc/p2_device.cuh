@@ -443,25 +443,6 @@ __device__ __forceinline__ void rows_extract(const View &a, uint32_t r_first, ui
     }
 }
 
-// Runtime (channels, plane) -> the templated unit and run routines.
-template <bool STATS, int UT>
-__device__ __forceinline__ void units_embed_any(const View &a, uint32_t k_first, uint32_t k_end,
-                                                uint32_t step, unsigned long long &changed,
-                                                unsigned long long &sse)
-{
-    switch (a.channels * 4 + a.plane) {
-    case 4: units_embed<1, 0, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 12: units_embed<3, 0, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 13: units_embed<3, 1, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 14: units_embed<3, 2, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 16: units_embed<4, 0, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 17: units_embed<4, 1, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 18: units_embed<4, 2, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    case 19: units_embed<4, 3, STATS, UT>(a, k_first, k_end, step, changed, sse); break;
-    default: break;
-    }
-}
-
 __device__ __forceinline__ void runs_extract_any(const View &a, uint64_t k_first, uint64_t k_end,
                                                  uint64_t step)
 {
