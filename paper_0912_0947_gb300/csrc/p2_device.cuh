@@ -443,6 +443,7 @@ __device__ __forceinline__ void rows_extract(const View &a, uint32_t r_first, ui
     }
 }
 
+// Runtime (channels, plane) -> the templated run routine.
 __device__ __forceinline__ void runs_extract_any(const View &a, uint64_t k_first, uint64_t k_end,
                                                  uint64_t step)
 {
