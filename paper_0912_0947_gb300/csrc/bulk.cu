@@ -537,6 +537,7 @@ cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_
         const uint64_t fit = C >= 32 ? (C - 32) / 8 : 0;
         max_len = fit < cap ? fit : cap;
     }
+    e.x.max_vec = max_len >> 1;
     const int v = clamp_v(sh.vec);
     const void *k = extract_kernel(v);
     cudaError_t err = allow_ring(k);

@@ -504,6 +504,7 @@ struct ExtractArgs {
     uint32_t header;
     uint32_t msg_even;
     stego_result *res;
+    uint64_t max_vec; // most 16-byte vectors the call can need (length bound)
 };
 
 // Length and status of the call: from the header (read by warp 0 of every

@@ -106,18 +106,46 @@ __global__ void __launch_bounds__(512) embed_bytes(EmbedArgs e)
 using s1::ExtractArgs;
 using s1::extract_prologue;
 
-// Vector path: stego 16-byte aligned.
+// Vector path: stego 16-byte aligned.  The first round's loads are issued
+// before the header is read (bounded by the longest message the call can
+// produce, so they stay inside the stego); the round is then written for the
+// header's length.  Later rounds: whole rounds, then the remainder spread
+// one vector per thread as in embed_vec.
 template <int V>
 __global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
 {
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x;
+    const uint64_t round = (uint64_t)gridDim.x * blockDim.x * V;
+    const uint4 *__restrict__ src =
+        reinterpret_cast<const uint4 *>(a.st + (a.header ? 32u : 0u));
+    uint4 c[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        const uint64_t v = first + (uint64_t)u * blockDim.x;
+        if (v < a.max_vec)
+            c[u] = __ldcs(src + v);
+    }
     ExtractView x;
     if (extract_prologue(a, x) != STEGO_OK)
         return;
     const uint64_t nvec = x.len >> 1;
-    const uint64_t round = (uint64_t)gridDim.x * blockDim.x * V;
-    const uint64_t whole = nvec / round * round; // the remainder spread as in embed_vec
-    s1::extract_vec_range<V>(x, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x, whole, round);
-    s1::extract_vec_range<1>(x, whole + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nvec,
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        const uint64_t v = first + (uint64_t)u * blockDim.x;
+        if (v >= nvec)
+            continue;
+        const uint32_t pair = s1::gather16(c[u]);
+        if (x.msg_even) {
+            *reinterpret_cast<unsigned short *>(x.msg + 2 * v) = (unsigned short)pair;
+        } else {
+            x.msg[2 * v] = (uint8_t)pair;
+            x.msg[2 * v + 1] = (uint8_t)(pair >> 8);
+        }
+    }
+    const uint64_t whole = nvec / round * round;
+    s1::extract_vec_range<V>(x, first + round, whole, round);
+    const uint64_t rest = whole > round ? whole : round; // vectors below: done above
+    s1::extract_vec_range<1>(x, rest + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nvec,
                              (uint64_t)gridDim.x * blockDim.x);
     if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0)
         s1::extract_one(x, x.len - 1);
@@ -219,6 +247,7 @@ cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap
         const uint64_t fit = C >= 32 ? (C - 32) / 8 : 0;
         max_len = fit < cap ? fit : cap;
     }
+    a.max_vec = max_len >> 1;
     const int T = sh.threads;
     void *args[] = {&a};
     if (aligned16(st) && bulk_stages(sh))
