@@ -294,7 +294,11 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cover_h, msg_h = cover.cpu().numpy(), msg.cpu().numpy()
-        cpu = run_cpu_baseline(cover_h, msg_h, budget_s=args.cpu_seconds)
+        embed()  # the timed configuration's outputs, compared with the oracle's
+        extract()
+        torch.cuda.synchronize(dev)
+        cpu = run_cpu_baseline(cover_h, msg_h, budget_s=args.cpu_seconds,
+                               gpu_stego=stego.cpu().numpy(), gpu_msg=out.cpu().numpy())
         cpu["all_cores"] = run_cpu_all_cores(cover_h, msg_h, budget_s=args.cpu_seconds / 2)
 
     if rank != 0:
@@ -865,8 +869,9 @@ def run_e2e(args, S, torch, dev, stream, cover_d, msg_d, C, m):
 # CPU oracle (baseline leg and reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_round_trip(O, cover, msg):
-    """One embed + extract of (cover, msg) by the oracle; returns seconds."""
+def oracle_round_trip(O, cover, msg, keep=None):
+    """One embed + extract of (cover, msg) by the oracle; returns seconds.
+    With `keep` (a dict), the stego and message it produced are stored."""
     import numpy as np
     out = np.empty_like(cover)
     t0 = time.perf_counter()
@@ -874,6 +879,8 @@ def oracle_round_trip(O, cover, msg):
     st2, got = O.stream1_extract(out, cap=msg.size, header=True)
     dt = time.perf_counter() - t0
     assert st == 0 and st2 == 0 and got.size == msg.size
+    if keep is not None:
+        keep["stego"], keep["msg"] = out, got
     return dt
 
 
@@ -900,17 +907,25 @@ def host_cpu() -> str:
     return "%s, %d cores" % (name or "unknown CPU", os.cpu_count() or 0)
 
 
-def run_cpu_baseline(cover, msg, budget_s=12.0):
+def run_cpu_baseline(cover, msg, budget_s=12.0, gpu_stego=None, gpu_msg=None):
+    """The oracle's round trips on one host core.  With the GPU's stego and
+    extracted message of the timed configuration, the last round trip's
+    outputs are compared with them byte for byte (`matches_gpu`)."""
+    import numpy as np
     import oracle
     O = oracle.load()
-    reps, elapsed = 0, 0.0
+    reps, elapsed, keep = 0, 0.0, {}
     while elapsed < budget_s and reps < 50:
-        elapsed += oracle_round_trip(O, cover, msg)
+        elapsed += oracle_round_trip(O, cover, msg, keep)
         reps += 1
-    return {"value": round(2.0 * cover.size * reps / elapsed / 1e9, 4), "unit": UNIT,
-            "cores": 1, "kind": "oracle", "host": host_cpu(),
-            "sample": "%d embed+extract round trips of the whole %d-byte cover "
-                      "(single-threaded C oracle, %.1f s)" % (reps, cover.size, elapsed)}
+    out = {"value": round(2.0 * cover.size * reps / elapsed / 1e9, 4), "unit": UNIT,
+           "cores": 1, "kind": "oracle", "host": host_cpu(),
+           "sample": "%d embed+extract round trips of the whole %d-byte cover "
+                     "(single-threaded C oracle, %.1f s)" % (reps, cover.size, elapsed)}
+    if gpu_stego is not None:
+        out["matches_gpu"] = bool(np.array_equal(keep["stego"], gpu_stego) and
+                                  np.array_equal(keep["msg"], gpu_msg))
+    return out
 
 
 def run_cpu_all_cores(cover, msg, budget_s=6.0):

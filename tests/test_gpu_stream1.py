@@ -300,3 +300,37 @@ def test_same_misalignment_full_size(S, O):
     r = S.read_result(res)
     assert (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
     assert S.read_result(res2)["msg_bytes"] == m and torch.equal(out, msg)
+
+
+def test_single_8192_autotuned_shapes(S, O):
+    """The full-size cover in the launch shapes the autotuner installs for
+    the benchmark (register or staged kernels), every byte against the
+    oracle."""
+    from paper_0912_0947_gb300 import autotune as AT
+    w = synth.single_8192()
+    cover = w.cover("cuda")
+    msg = w.message("cuda")
+    stego = torch.empty_like(cover)
+    out = torch.empty(w.msg_bytes, dtype=torch.uint8, device="cuda")
+    res, res2 = S.new_result(), S.new_result()
+    emb = lambda: S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res)
+    ext = lambda: S.stego_extract(stego, out, 0, S.HEADER_BE32, res2)
+    old = (S.stego_get_tune(S.OP_EMBED), S.stego_get_tune(S.OP_EXTRACT))
+    try:
+        emb()
+        for op, fn in ((S.OP_EMBED, emb), (S.OP_EXTRACT, ext)):
+            AT.autotune(op, fn, cover.numel(), reps=3, use_cache=False)
+        stego.zero_()
+        out.zero_()
+        emb()
+        ext()
+        c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+        st, want = O.stream1_embed(c_h, m_h, header=True)
+        assert st == 0 and np.array_equal(stego.cpu().numpy(), want)
+        r = S.read_result(res)
+        assert (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+        assert S.read_result(res2)["msg_bytes"] == w.msg_bytes
+        assert np.array_equal(out.cpu().numpy(), m_h)
+    finally:
+        S.stego_set_tune(S.OP_EMBED, old[0])
+        S.stego_set_tune(S.OP_EXTRACT, old[1])
