@@ -730,7 +730,9 @@ def run_small_leg(S, AT, torch, dev, synth, reps=25, burst=1000):
     latency bound.  Cold = L2 flushed before each call, warm = after an
     untimed run of the same call (both with the call queued before its start
     event); back to back = `burst` calls between two events (device time per
-    call, launch gaps included); enqueue = host time per API call."""
+    call, launch gaps included); enqueue = host time per API call;
+    graph = one embed + one extract captured in a CUDA graph, replayed back
+    to back (device time per pair)."""
     w = synth.single_512()
     C, m = w.cover_bytes, w.msg_bytes
     cover, msg = w.cover(dev), w.message(dev)
@@ -773,6 +775,30 @@ def run_small_leg(S, AT, torch, dev, synth, reps=25, burst=1000):
                    "cover_gbs_cold": round(C / (cold * 1e-6) / 1e9, 1),
                    "cover_gbs_back_to_back": round(C / (b2b * 1e-6) / 1e9, 1)}
     assert torch.equal(out, msg)
+    # one embed + one extract captured into a CUDA graph, replayed back to back
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        emb_s = lambda: S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res_e,
+                                      stream=side)
+        ext_s = lambda: S.stego_extract(stego, out, 0, S.HEADER_BE32, res_x, stream=side)
+        emb_s()
+        ext_s()
+    torch.cuda.synchronize(dev)
+    with torch.cuda.graph(g, stream=side):
+        emb_s()
+        ext_s()
+    out.zero_()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(burst):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(out, msg)
+    r["graph_embed_extract_us"] = round(e0.elapsed_time(e1) * 1e3 / burst, 2)
     return r
 
 
