@@ -109,3 +109,21 @@ def test_product_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "stego_oracle" not in text, f
+
+
+def test_header_compiles_as_c():
+    """include/stego.h is plain C: the C example that uses it compiles with
+    gcc (syntax only, no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not gcc or not os.path.exists(nvcc):
+        pytest.skip("gcc or the CUDA toolkit not available")
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        os.path.join(here, "c", "abi_roundtrip.c"),
+                        "-I" + os.path.join(os.path.dirname(here), "include"),
+                        "-I" + os.path.join(cuda, "include")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
