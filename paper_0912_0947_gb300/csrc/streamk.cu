@@ -249,9 +249,9 @@ __device__ __forceinline__ void scatter_xor(uint32_t (&w)[4 * CH], const uint32_
 
 // Word i (carrying bytes 4i..4i+3, field in each byte's low K bits) of a
 // unit whose stream window is X (stream bytes big-endian, the first in bits
-// 56..63).  K = 1, 2, 4 fill the four byte lanes from replicated stream
-// bytes with fixed per-lane shifts; K = 3 (fields across byte boundaries)
-// cuts the 64-bit window field by field.
+// 56..63).  K = 1, 4 fill the four byte lanes from replicated stream bytes
+// with fixed per-lane shifts, K = 2 with one multiply; K = 3 (fields across
+// byte boundaries) takes each word's 12 bits and cuts them field by field.
 template <int K>
 __device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
 {
@@ -261,11 +261,11 @@ __device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
         const uint32_t r = __byte_perm(hi, 0u, i < 2 ? 0x3333u : 0x2222u);
         return (i & 1) ? s1::spread_lo(r) : s1::spread_hi(r);
     } else if constexpr (K == 2) {
-        // stream byte i; lane l takes its bits 7-2l and 6-2l
-        const uint32_t sel = 0x3333u - 0x1111u * (uint32_t)i;
-        const uint32_t r = __byte_perm(hi, 0u, sel);
-        return ((r >> 6) & 0x03u) | ((r >> 4) & 0x0300u) | ((r >> 2) & 0x030000u) |
-               (r & 0x03000000u);
+        // stream byte i; lane l takes its bits 7-2l and 6-2l: the products
+        // b << 10l occupy disjoint bit ranges, and bits 8l+6, 8l+7 of their
+        // sum hold pair l (b's bits 7-2l, 6-2l)
+        const uint32_t b = (hi >> (24 - 8 * i)) & 0xFFu;
+        return ((b * 0x40100401u) >> 6) & 0x03030303u;
     } else if constexpr (K == 4) {
         // stream bytes 2i, 2i+1; lanes take high nibble, low nibble, high, low
         const uint32_t r = __byte_perm(i < 2 ? hi : lo, 0u, (i & 1) ? 0x0011u : 0x2233u);
