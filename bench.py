@@ -261,7 +261,8 @@ def run_ours(args, rank, world, local_rank):
     legs = {}
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
                                                          "batched_video_paper2", "paper2",
-                                                         "streamk", "serving", "small"}
+                                                         "streamk", "serving", "small",
+                                                         "extract_gather"}
     if args.no_batched:
         want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk"}
     if args.no_serving:
@@ -277,6 +278,9 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.empty_cache()
     if rank == 0 and "streamk" in want:
         legs["streamk"] = run_streamk_leg(S, AT, torch, dev, synth)
+        torch.cuda.empty_cache()
+    if rank == 0 and "extract_gather" in want:
+        legs["extract_gather"] = run_extract_gather_leg(S, AT, torch, dev, synth)
         torch.cuda.empty_cache()
     if rank == 0 and "small" in want:
         legs["small_512x512x3"] = run_small_leg(S, AT, torch, dev, synth)
@@ -724,6 +728,43 @@ def run_streamk_leg(S, AT, torch, dev, synth):
     return out
 
 
+def run_extract_gather_leg(S, AT, torch, dev, synth,
+                           shapes=((128, 4, 0, 0), (256, 4, 0, 0), (512, 4, 0, 0),
+                                   (128, 4, 8, 0), (256, 2, 4, 0), (512, 8, 2, 0))):
+    """The full-capacity 8192x8192x3 extraction by the vector kernel
+    (stego_extract: 16 stego bytes per lane, one multiply per four bytes)
+    and by the ballot kernel (stego_extract_ballot: one stego byte per lane,
+    one ballot per message word), same launch shapes, L2 flushed."""
+    w = synth.single_8192()
+    cover, msg = w.cover(dev), w.message(dev)
+    stego = torch.empty_like(cover)
+    S.stego_embed(cover, stego, msg, S.HEADER_BE32)
+    out = torch.empty(w.msg_bytes, dtype=torch.uint8, device=dev)
+    res = S.new_result(dev)
+    flush = AT.Flusher(dev)
+    old = S.stego_get_tune(S.OP_EXTRACT)
+    table = []
+    try:
+        for sh in shapes:
+            S.stego_set_tune(S.OP_EXTRACT, sh)
+            tv = AT.time_call(lambda: S.stego_extract(stego, out, 0, S.HEADER_BE32, res), flush, 15)
+            tb = AT.time_call(lambda: S.stego_extract_ballot(stego, out, 0, S.HEADER_BE32, res),
+                              flush, 15)
+            table.append((list(sh[:3]), round(tv, 2), round(tb, 2)))
+        torch.cuda.synchronize()
+        assert torch.equal(out, msg)
+    finally:
+        S.stego_set_tune(S.OP_EXTRACT, old)
+    T = 8 * (w.msg_bytes + 4)
+    peak, _ = hbm_peak()
+    bv, bb = min(t[1] for t in table), min(t[2] for t in table)
+    frac = lambda us: round((T + T // 8) / (us * 1e-6) / 1e9 / peak, 4)
+    return {"workload": "8192x8192x3 cover, full one-bit capacity, header extraction",
+            "vector_best_us": bv, "ballot_best_us": bb,
+            "hbm_frac": {"vector": frac(bv), "ballot": frac(bb)},
+            "shapes_vector_ballot_us": table}
+
+
 def run_small_leg(S, AT, torch, dev, synth, reps=25, burst=1000):
     """The 512x512x3 cover (786,432 bytes) with a 32,768-byte message behind
     the header: the whole working set fits the L2, so the time is launch and
@@ -1050,7 +1091,8 @@ def main():
                     help="frames in the video batched leg (default 600)")
     ap.add_argument("--legs", default="",
                     help="comma list of extra legs: batched_uneven,batched_video,"
-                         "batched_video_paper2,paper2,streamk,serving,small, or none "
+                         "batched_video_paper2,paper2,streamk,serving,small,extract_gather, "
+                         "or none "
                          "(default all)")
     args = ap.parse_args()
     if args.warmup < 3:

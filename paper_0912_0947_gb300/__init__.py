@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
         L.stego_embed.restype = _int
         L.stego_extract.argtypes = [_vp, _u64, _vp, _u64, _u64, ctypes.POINTER(Geom), _u32, _vp, _vp]
         L.stego_extract.restype = _int
+        L.stego_extract_ballot.argtypes = [_vp, _u64, _vp, _u64, _u64, ctypes.POINTER(Geom), _u32, _vp, _vp]
+        L.stego_extract_ballot.restype = _int
         L.stego_changed_bytes.argtypes = [_vp, _vp, _u64, _vp, _vp]
         L.stego_changed_bytes.restype = _int
         L.stego_batched_workspace_bytes.argtypes = [_u32]
@@ -287,6 +289,19 @@ def stego_extract(stego, msg, msg_len: int, flags: int, result=None, geom=None,
                              int(msg_len), _geom(geom), int(flags), r,
                              _stream_ptr(stream, stego.device))
     _check(st, "stego_extract")
+
+
+def stego_extract_ballot(stego, msg, msg_len: int, flags: int, result=None, geom=None,
+                         stream=None) -> None:
+    """stego_extract computed by the ballot-gather kernel (one-bit stream
+    layout only)."""
+    s = _dev_ptr(stego, "stego")
+    m = _dev_ptr(msg, "msg") if msg is not None else None
+    r = _dev_ptr(result, "result", torch.int64)
+    st = lib().stego_extract_ballot(s, stego.numel(), m, 0 if msg is None else msg.numel(),
+                                    int(msg_len), _geom(geom), int(flags), r,
+                                    _stream_ptr(stream, stego.device))
+    _check(st, "stego_extract_ballot")
 
 
 def stego_changed_bytes(a, b, out2, stream=None) -> None:

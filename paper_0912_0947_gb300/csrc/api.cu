@@ -350,9 +350,15 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
                                 slot));
 }
 
-int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
-                  uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom, uint32_t flags,
-                  stego_result *d_result, void *stream)
+} // extern "C"
+
+namespace {
+
+// stego_extract and stego_extract_ballot: validation and dispatch; with
+// `ballot` the one-bit stream layout's kernel packs the message by ballots.
+int extract_impl(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
+                 uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom, uint32_t flags,
+                 stego_result *d_result, void *stream, bool ballot)
 {
     const uint32_t known = STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_PLANE_ONLY |
                            STEGO_BITS_MASK;
@@ -363,6 +369,8 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
     const bool plane_only = (flags & STEGO_PLANE_ONLY) != 0;
     const uint32_t k = bits_of(flags);
     if (layout != STEGO_LAYOUT_STREAM1 && layout != STEGO_LAYOUT_PAPER2)
+        return STEGO_E_INVAL;
+    if (ballot && (layout != STEGO_LAYOUT_STREAM1 || plane_only || k != 1))
         return STEGO_E_INVAL;
     if (layout == STEGO_LAYOUT_PAPER2 && (header || plane_only || k != 1))
         return STEGO_E_INVAL;
@@ -390,6 +398,9 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
         if (variant)
             return cuda_status(sk_extract(d_stego, cover_bytes, k, plane_only, geom, d_msg,
                                           msg_cap, 0, true, d_result, sh, s));
+        if (ballot)
+            return cuda_status(s1_extract_ballot(d_stego, cover_bytes, d_msg, msg_cap, 0, true,
+                                                 d_result, sh, s));
         return cuda_status(s1_extract(d_stego, cover_bytes, d_msg, msg_cap, 0, true, d_result, sh, s));
     }
     uint64_t cap = 0;
@@ -408,9 +419,32 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
     if (variant)
         return cuda_status(sk_extract(d_stego, cover_bytes, k, plane_only, geom, d_msg, msg_cap,
                                       msg_len, false, d_result, sh, s));
+    if (layout == STEGO_LAYOUT_STREAM1 && ballot)
+        return cuda_status(s1_extract_ballot(d_stego, cover_bytes, d_msg, msg_cap, msg_len, false,
+                                             d_result, sh, s));
     if (layout == STEGO_LAYOUT_STREAM1)
         return cuda_status(s1_extract(d_stego, cover_bytes, d_msg, msg_cap, msg_len, false, d_result, sh, s));
     return cuda_status(p2_extract(d_stego, *geom, d_msg, msg_len, d_result, sh, s));
+}
+
+} // namespace
+
+extern "C" {
+
+int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
+                  uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom, uint32_t flags,
+                  stego_result *d_result, void *stream)
+{
+    return extract_impl(d_stego, cover_bytes, d_msg, msg_cap, msg_len, geom, flags, d_result,
+                        stream, false);
+}
+
+int stego_extract_ballot(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
+                         uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom,
+                         uint32_t flags, stego_result *d_result, void *stream)
+{
+    return extract_impl(d_stego, cover_bytes, d_msg, msg_cap, msg_len, geom, flags, d_result,
+                        stream, true);
 }
 
 int stego_changed_bytes(const uint8_t *d_a, const uint8_t *d_b, uint64_t n, uint64_t *d_out2,

@@ -109,6 +109,12 @@ cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_onl
                        const stego_geom *g, uint8_t *msg, uint64_t cap, uint64_t raw_len,
                        bool header, stego_result *res, const Shape &sh, cudaStream_t s);
 
+// STREAM1 extraction with the message packed by warp ballots (one stego
+// byte per lane; ballot.cu); same arguments and results as s1_extract.
+cudaError_t s1_extract_ballot(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
+                              uint64_t raw_len, bool header, stego_result *res, const Shape &sh,
+                              cudaStream_t s);
+
 // STREAM1 kernels staged through shared memory with bulk asynchronous
 // copies (bulk.cu); same arguments and results as s1_embed / s1_extract.
 // Usable with 16-byte aligned buffers when bulk_stages(sh) >= 2: a shape
