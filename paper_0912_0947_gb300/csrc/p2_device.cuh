@@ -143,12 +143,11 @@ __device__ __forceinline__ void load16(const uint8_t *__restrict__ mp, uint32_t 
 }
 
 // Changed bytes and squared error of two vectors that differ only in the
-// low two bits of some bytes.
-__device__ __forceinline__ void pair_stats(const uint4 &o, const uint4 &c,
-                                           unsigned long long &changed, unsigned long long &sse)
+// low two bits of some bytes, added to 32-bit per-unit counts.
+__device__ __forceinline__ void pair_stats(const uint4 &o, const uint4 &c, uint32_t &n,
+                                           uint32_t &s)
 {
     const uint32_t ow[4] = {o.x, o.y, o.z, o.w}, cw[4] = {c.x, c.y, c.z, c.w};
-    uint32_t n = 0, s = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t x = ow[q] ^ cw[q];
@@ -156,8 +155,6 @@ __device__ __forceinline__ void pair_stats(const uint4 &o, const uint4 &c,
         const uint32_t d = __vabsdiffu4(ow[q] & 0x03030303u, cw[q] & 0x03030303u);
         s = __dp4a(d, d, s);
     }
-    changed += n;
-    sse += s;
 }
 
 // One pass over units k = k_first + i*step (+ u*blockDim.x, u < UT),
@@ -249,9 +246,12 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
                 slow_unit<CH, PLANE, 0>(o, colf[u], L[u], mrow[u]);
             }
             if (STATS && mode[u]) {
+                uint32_t n = 0, sq = 0; // at most 16 pairs changed, 9 each
 #pragma unroll
                 for (int q = 0; q < CH; ++q)
-                    pair_stats(o[q], c[u][q], changed, sse);
+                    pair_stats(o[q], c[u][q], n, sq);
+                changed += n;
+                sse += sq;
             }
 #pragma unroll
             for (int q = 0; q < CH; ++q)
