@@ -255,7 +255,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
     if (rank == 0 or world > 1) and args.e2e_steps > 0:
-        e2e = run_e2e_zero_copy(args, S, torch, dev, stream, cover, msg, C, m)
+        e2e = run_e2e_pipelined(args, S, torch, dev, stream, cover, msg, C, m)
+        e2e["zero_copy_host_stego"] = run_e2e_zero_copy(args, S, torch, dev, stream, cover,
+                                                        msg, C, m)
         e2e["explicit_copy"] = run_e2e(args, S, torch, dev, stream, cover, msg, C, m)
     # ---- batched vs one launch per image -----------------------------------------
     legs = {}
@@ -883,6 +885,81 @@ def run_e2e_zero_copy(args, S, torch, dev, stream, cover_d, msg_d, C, m):
     return {"value": round(2.0 * C / (ms * 1e-3) / 1e9, 2), "unit": UNIT,
             "ms_per_step": round(ms, 4), "steps": n, "mode": "zero-copy (pinned host buffers)",
             "h2d_bytes_per_step": 2 * C + m, "d2h_bytes_per_step": C + m + 64}
+
+
+def run_e2e_pipelined(args, S, torch, dev, stream, cover_d, msg_d, C, m, nslots=2):
+    """The step through the public API with host inputs and outputs,
+    pipelined over three streams and two device slots: host->device copies
+    of step i+1's cover and message run while step i's embed and extract
+    run on HBM and step i-1's stego and message are copied back, so both
+    link directions and the kernels overlap.  Every input byte crosses
+    host->device and every output byte device->host inside the timed
+    region."""
+    cover_h = cover_d.cpu().pin_memory()
+    msg_h = msg_d.cpu().pin_memory()
+    stego_h = torch.empty(C, dtype=torch.uint8).pin_memory()
+    out_h = torch.empty(m, dtype=torch.uint8).pin_memory()
+    res_h = torch.empty((nslots, 2, 4), dtype=torch.int64).pin_memory()
+    c_d = [torch.empty(C, dtype=torch.uint8, device=dev) for _ in range(nslots)]
+    m_d = [torch.empty(m, dtype=torch.uint8, device=dev) for _ in range(nslots)]
+    s_d = [torch.empty(C, dtype=torch.uint8, device=dev) for _ in range(nslots)]
+    o_d = [torch.empty(m, dtype=torch.uint8, device=dev) for _ in range(nslots)]
+    r_d = [S.new_result(dev, n=2) for _ in range(nslots)]  # [embed, extract]
+    s_h, s_k, s_c = (torch.cuda.Stream(dev) for _ in range(3))
+    done_h = [torch.cuda.Event() for _ in range(nslots)]
+    done_k = [torch.cuda.Event() for _ in range(nslots)]
+    done_c = [torch.cuda.Event() for _ in range(nslots)]
+    for st in (s_h, s_k, s_c):
+        st.wait_stream(stream)
+
+    def step(i):
+        j = i % nslots
+        if i >= nslots:
+            s_h.wait_event(done_k[j])  # the slot's inputs were consumed
+        with torch.cuda.stream(s_h):
+            c_d[j].copy_(cover_h, non_blocking=True)
+            m_d[j].copy_(msg_h, non_blocking=True)
+        done_h[j].record(s_h)
+        s_k.wait_event(done_h[j])
+        if i >= nslots:
+            s_k.wait_event(done_c[j])  # the slot's outputs were copied back
+        S.stego_embed(c_d[j], s_d[j], m_d[j], S.HEADER_BE32 | S.FUSE_STATS, r_d[j][0],
+                      stream=s_k)
+        S.stego_extract(s_d[j], o_d[j], 0, S.HEADER_BE32, r_d[j][1], stream=s_k)
+        done_k[j].record(s_k)
+        s_c.wait_event(done_k[j])
+        with torch.cuda.stream(s_c):
+            stego_h.copy_(s_d[j], non_blocking=True)
+            out_h.copy_(o_d[j], non_blocking=True)
+            res_h[j].copy_(r_d[j], non_blocking=True)
+        done_c[j].record(s_c)
+
+    for i in range(nslots):
+        step(i)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(out_h, msg_h) and int(res_h[nslots - 1][1][2]) == m
+    n = args.e2e_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_h)
+    s_k.wait_event(e0)
+    s_c.wait_event(e0)
+    for i in range(n):
+        step(i)
+    s_h.wait_stream(s_k)
+    s_h.wait_stream(s_c)
+    e1.record(s_h)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / n
+    want = torch.empty_like(cover_d)
+    S.stego_embed(cover_d, want, msg_d, S.HEADER_BE32)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(stego_h, want.cpu()), "pipelined stego differs"
+    assert torch.equal(out_h, msg_h), "pipelined message differs"
+    return {"value": round(2.0 * C / (ms * 1e-3) / 1e9, 2), "unit": UNIT,
+            "ms_per_step": round(ms, 4), "steps": n,
+            "mode": "pipelined copies: H2D of step i+1, kernels of step i, D2H of step i-1 "
+                    "on three streams, two device slots",
+            "h2d_bytes_per_step": C + m, "d2h_bytes_per_step": C + m + 64}
 
 
 def run_e2e(args, S, torch, dev, stream, cover_d, msg_d, C, m):
