@@ -16,6 +16,11 @@
 namespace stego {
 namespace {
 
+// The installed launch shapes are tuned for the one-bit kernels; these
+// kernels (other register counts) take as many resident CTAs as occupancy
+// allows instead of a tuned CTA count.
+constexpr int kAnyCtas = 0;
+
 using p2::View;
 
 struct P2Args {
@@ -103,7 +108,7 @@ P2Args make_args(const uint8_t *src, uint8_t *dst, const stego_geom &g, const ui
 
 int row_grid(const void *k, const Shape &sh, uint32_t rows)
 {
-    return persistent_grid(k, sh.threads, 0, sh.ctas_per_sm, rows ? rows : 1, 1);
+    return persistent_grid(k, sh.threads, 0, kAnyCtas, rows ? rows : 1, 1);
 }
 
 template <bool STATS, bool INPLACE>
@@ -170,7 +175,7 @@ cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geo
     const void *k = stats ? units_kernel<true, false>(g.channels, g.plane)
                           : units_kernel<false, false>(g.channels, g.plane);
     const uint64_t nunits = (uint64_t)(g.width / 16u) * g.height;
-    const int grid = persistent_grid(k, kUnitThreads, 0, sh.ctas_per_sm, nunits ? nunits : 1,
+    const int grid = persistent_grid(k, kUnitThreads, 0, kAnyCtas, nunits ? nunits : 1,
                                      (uint64_t)kUnitThreads * kUnitsPerThread);
     void *args[] = {&a};
     return cudaLaunchKernel(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
@@ -188,7 +193,7 @@ cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
         const void *k = stats ? units_kernel<true, true>(g.channels, g.plane)
                               : units_kernel<false, true>(g.channels, g.plane);
         const uint64_t nunits = (uint64_t)(g.width / 16u) * a.v.R;
-        const int grid = persistent_grid(k, kUnitThreads, 0, sh.ctas_per_sm,
+        const int grid = persistent_grid(k, kUnitThreads, 0, kAnyCtas,
                                          nunits ? nunits : 1,
                                          (uint64_t)kUnitThreads * kUnitsPerThread);
         void *args[] = {&a};
@@ -208,7 +213,7 @@ cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uin
     if (p2::unit_channels(g.channels)) {
         const void *k = extract_units_kernel(g.channels, g.plane);
         const uint64_t runs = (uint64_t)((a.v.Q + 15) / 16) * a.v.R;
-        const int grid = persistent_grid(k, sh.threads, 0, sh.ctas_per_sm, runs ? runs : 1,
+        const int grid = persistent_grid(k, sh.threads, 0, kAnyCtas, runs ? runs : 1,
                                          (uint64_t)sh.threads);
         return cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
     }

@@ -31,6 +31,11 @@
 namespace stego {
 namespace {
 
+// The installed launch shapes are tuned for the one-bit kernels; these
+// kernels (other register counts) take as many resident CTAs as occupancy
+// allows instead of a tuned CTA count.
+constexpr int kAnyCtas = 0;
+
 struct KView {
     const uint8_t *cover; // embed: cover; extract: stego
     uint8_t *stego;       // embed output
@@ -707,7 +712,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
                                  : embed_units_kernel<false>(k, a.channels, a.plane);
         const uint64_t nunits = a.n_carry >> 4;
         const int per_thread = a.channels == 1 ? kEmbedAllBytesUnits : 1;
-        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nunits ? nunits : 1,
+        const int grid = persistent_grid(kern, T, 0, kAnyCtas, nunits ? nunits : 1,
                                          (uint64_t)T * per_thread);
         return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
     }
@@ -720,7 +725,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     }
     a.n_carry = plane_only ? t_carry : (inplace ? t_carry : C);
     const void *kern = stats ? (const void *)embedk_bytes<true> : (const void *)embedk_bytes<false>;
-    const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, a.n_carry ? a.n_carry : 1,
+    const int grid = persistent_grid(kern, T, 0, kAnyCtas, a.n_carry ? a.n_carry : 1,
                                      (uint64_t)T * 16);
     return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
 }
@@ -755,12 +760,12 @@ cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_onl
         const void *kern = extract_units_kernel(k, a.channels, a.plane);
         const uint64_t nunits = (max_len + 4 + 2 * k - 1) / (2 * k);
         const int per_thread = a.channels == 1 ? kExtractAllBytesUnits : 1;
-        const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, nunits ? nunits : 1,
+        const int grid = persistent_grid(kern, T, 0, kAnyCtas, nunits ? nunits : 1,
                                          (uint64_t)T * per_thread);
         return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
     }
     const void *kern = (const void *)extractk_bytes;
-    const int grid = persistent_grid(kern, T, 0, sh.ctas_per_sm, max_len ? max_len : 1, (uint64_t)T);
+    const int grid = persistent_grid(kern, T, 0, kAnyCtas, max_len ? max_len : 1, (uint64_t)T);
     return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
 }
 
