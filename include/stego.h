@@ -128,8 +128,12 @@ typedef struct stego_result {
  *   msg_bytes    embed: message length; extract: capacity of msg.
  *   msg_len      extract without a header (raw STREAM1, PAPER2): bytes to
  *                extract; ignored otherwise.
- *   flags        layout and header flags as for the single calls
- *                (STEGO_FUSE_STATS is taken from the batched call instead).
+ *   flags        STEGO_LAYOUT_STREAM1 (one bit per byte, with or without
+ *                STEGO_HEADER_BE32) or STEGO_LAYOUT_PAPER2; STEGO_FUSE_STATS
+ *                is taken from the batched call instead.  The k-bit and
+ *                one-plane stream options (STEGO_BITS(k), k > 1, and
+ *                STEGO_PLANE_ONLY) are single-cover only: such a
+ *                descriptor gets STEGO_E_INVAL in its result.
  *   geom         PAPER2 geometry. */
 typedef struct stego_desc {
     const uint8_t *cover;

@@ -398,3 +398,28 @@ def test_batched_paper_layout_video(S, O):
     descs = S.descs_to_device(S.pack_descs(recs))
     S.stego_extract_batched(descs, F, res, 0, ws)
     assert torch.equal(out, stream)
+
+
+def test_kbit_descriptors_refused_per_cover(S, O):
+    """k-bit and one-plane stream descriptors are single-cover only: in a
+    batch they get STEGO_E_INVAL in their own result and are not written;
+    the other covers of the batch embed normally."""
+    rng = np.random.default_rng(77)
+    covers = [rng.integers(0, 256, 4096, dtype=np.uint8) for _ in range(3)]
+    msgs = [rng.integers(0, 256, 100, dtype=np.uint8) for _ in range(3)]
+    flags = [S.HEADER_BE32, S.HEADER_BE32 | S.BITS(2), S.HEADER_BE32 | S.PLANE_ONLY]
+    geo = [{}, {}, dict(width=32, height=32, channels=4, plane=0)]
+    cv = [torch.from_numpy(c).cuda() for c in covers]
+    sv = [torch.full((4096,), 0x5A, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    mv = [torch.from_numpy(m).cuda() for m in msgs]
+    recs = [dict(cover=cv[i], stego=sv[i], msg=mv[i], cover_bytes=4096, msg_bytes=100,
+                 flags=flags[i], **geo[i]) for i in range(3)]
+    d = S.descs_to_device(S.pack_descs(recs))
+    res = S.new_result(n=3)
+    ws = torch.empty(S.stego_batched_workspace_bytes(3), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(d, 3, res, 0, ws)
+    r = S.read_result(res)
+    assert r[0]["status"] == S.OK and r[1]["status"] == S.E_INVAL and r[2]["status"] == S.E_INVAL
+    st, want = O.stream1_embed(covers[0], msgs[0], header=True)
+    assert st == 0 and np.array_equal(sv[0].cpu().numpy(), want)
+    assert bool((sv[1] == 0x5A).all()) and bool((sv[2] == 0x5A).all())
