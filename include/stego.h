@@ -354,7 +354,9 @@ typedef struct stego_server_config {
 
 typedef struct stego_request {
     uint32_t op;           /* STEGO_OP_EMBED or STEGO_OP_EXTRACT            */
-    uint32_t flags;        /* STEGO_LAYOUT_STREAM1 [| STEGO_HEADER_BE32]    */
+    uint32_t flags;        /* STEGO_LAYOUT_STREAM1 [| STEGO_HEADER_BE32];   */
+                           /* other layouts and bits per byte complete with */
+                           /* STEGO_E_INVAL (a request has no geometry)     */
     const uint8_t *cover;  /* embed: cover; extract: stego image            */
     uint8_t *stego;        /* embed: output image                           */
     uint8_t *msg;          /* embed: message (read); extract: output buffer */

@@ -129,6 +129,10 @@ def test_budget_and_bad_requests(S):
     recs.append(dict(op=99, cover=covers[0], cover_bytes=C, tag=101))       # unknown op
     recs.append(dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=covers[1], stego=outs[1], msg=msg,
                      cover_bytes=C, msg_bytes=C // 8, tag=102))            # too long a message
+    recs.append(dict(op=S.OP_EMBED, flags=S.LAYOUT_PAPER2, cover=covers[2], stego=outs[2],
+                     msg=msg, cover_bytes=C, msg_bytes=10, tag=103))       # no geometry
+    recs.append(dict(op=S.OP_EMBED, flags=S.BITS(2) | S.HEADER_BE32, cover=covers[2],
+                     stego=outs[2], msg=msg, cover_bytes=C, msg_bytes=10, tag=104))  # k = 2
     budget = 5 * C  # two embeds of 2C + 1000 fit, a third does not
     srv = S.Server(slots=3, max_batch=8, budget_bytes=budget)
     srv.submit(S.Server.requests(recs))
@@ -136,12 +140,14 @@ def test_budget_and_bad_requests(S):
     comps = _by_tag(srv.poll())
     st = srv.stats()
     srv.close()
-    assert sorted(comps) == list(range(6)) + [100, 101, 102]
+    assert sorted(comps) == list(range(6)) + [100, 101, 102, 103, 104]
     for i in range(6):
         assert int(comps[i]["status"]) == 0
     assert int(comps[100]["status"]) == S.E_NOMEM
     assert int(comps[101]["status"]) == S.E_INVAL
     assert int(comps[102]["status"]) == S.E_CAPACITY
+    assert int(comps[103]["status"]) == S.E_INVAL
+    assert int(comps[104]["status"]) == S.E_INVAL
     assert 0 < st["peak_in_flight_bytes"] <= budget
     assert st["outstanding"] == 0
     torch.cuda.synchronize()
