@@ -459,8 +459,11 @@ __device__ __forceinline__ void paper_embed_tile(const stego_desc &D, const Desc
         const uint64_t units = (uint64_t)(inf.W / 16u) * (ip ? v.R : inf.H);
         const uint32_t k0 = (uint32_t)b0 + threadIdx.x;
         const uint32_t k1 = (uint32_t)(b1 < units ? b1 : units);
+        // one unit per thread, not staged through shared memory: under the
+        // 80-register cap the staged form spilled more and ran slower (600
+        // video frames: 1.53 against 1.26 ms)
         if (inf.channels == 3)
-            p2::units_embed<3, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
+            p2::units_embed<3, 0, STATS, 1, false, false>(v, k0, k1, blockDim.x, changed, sse);
         else
             p2::units_embed<1, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
         return;
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, 
 // the stream kernels): tiles of units, rows or runs, claimed like above.
 // Capped at 80 registers for three CTAs per SM: on 600 video frames the
 // embed with statistics went from 1.47 to 1.32 ms and the extract from 0.54
-// to 0.48 ms, although the statistics variant now spills 92 bytes.
+// to 0.48 ms, although the statistics variant spills (120 bytes).
 template <bool STATS>
 __global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *descs, uint32_t n,
                                                         stego_result *results, WsView ws)

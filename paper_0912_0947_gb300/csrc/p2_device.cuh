@@ -79,31 +79,170 @@ __device__ __forceinline__ uint32_t &unit_word(uint4 (&o)[CH])
     return W == 0 ? v.x : W == 1 ? v.y : W == 2 ? v.z : v.w;
 }
 
-// Pair of pixel T (0..15) from a SWAR pair array (pair t in byte t%4 of
-// word t/4) into the unit's plane byte.
-template <int CH, int PLANE, int T>
+template <int CH, int B>
+__device__ __forceinline__ uint32_t unit_word_c(const uint4 (&c)[CH])
+{
+    const uint4 &v = c[B >> 4];
+    constexpr int W = (B >> 2) & 3;
+    return W == 0 ? v.x : W == 1 ? v.y : W == 2 ? v.z : v.w;
+}
+
+// Compile-time plan of the byte moves between a unit's words and its pair
+// words (pair t in byte t%4 of pair word t/4; pixel t's plane byte is unit
+// byte t*CH + PLANE).
+struct UnitPlan {
+    int CH, PLANE;
+    // pixel whose plane byte is unit byte b, or -1
+    __host__ __device__ constexpr int pixel_at(int b) const
+    {
+        return (b >= PLANE && (b - PLANE) % CH == 0 && (b - PLANE) / CH < 16) ? (b - PLANE) / CH
+                                                                             : -1;
+    }
+    // unit word WD: mask of its plane pairs, and the first and last pair
+    // words it takes pairs from
+    __host__ __device__ constexpr uint32_t put_mask(int WD) const
+    {
+        uint32_t m = 0;
+        for (int b = 0; b < 4; ++b)
+            if (pixel_at(4 * WD + b) >= 0)
+                m |= 3u << (8 * b);
+        return m;
+    }
+    __host__ __device__ constexpr int put_qa(int WD) const
+    {
+        for (int b = 0; b < 4; ++b)
+            if (pixel_at(4 * WD + b) >= 0)
+                return pixel_at(4 * WD + b) >> 2;
+        return 0;
+    }
+    __host__ __device__ constexpr int put_qb(int WD) const
+    {
+        for (int b = 3; b >= 0; --b)
+            if (pixel_at(4 * WD + b) >= 0)
+                return pixel_at(4 * WD + b) >> 2;
+        return 0;
+    }
+    // byte_perm selector placing the pairs of unit word WD from pair words
+    // qa (selector 0-3) and qb (4-7); other bytes are masked off later
+    __host__ __device__ constexpr uint32_t put_sel(int WD) const
+    {
+        uint32_t s = 0;
+        for (int b = 0; b < 4; ++b) {
+            const int t = pixel_at(4 * WD + b);
+            const uint32_t d = t < 0 ? 0u : (uint32_t)((t >> 2) == put_qa(WD) ? (t & 3) : 4 + (t & 3));
+            s |= d << (4 * b);
+        }
+        return s;
+    }
+    // pair word Q, byte J: the unit word and byte holding pixel 4Q+J
+    __host__ __device__ constexpr int src_word(int Q, int J) const { return ((4 * Q + J) * CH + PLANE) >> 2; }
+    __host__ __device__ constexpr int src_byte(int Q, int J) const { return ((4 * Q + J) * CH + PLANE) & 3; }
+    // the k-th distinct unit word pair word Q reads (k = 0..3), or -1
+    __host__ __device__ constexpr int gather_src(int Q, int k) const
+    {
+        int n = 0;
+        for (int j = 0; j < 4; ++j) {
+            if (j > 0 && src_word(Q, j) == src_word(Q, j - 1))
+                continue;
+            if (n == k)
+                return src_word(Q, j);
+            ++n;
+        }
+        return -1;
+    }
+    // selector of the first gather step (distinct words 0 and 1) and of the
+    // step adding distinct word k >= 2 to what is gathered so far
+    __host__ __device__ constexpr uint32_t gather_sel0(int Q) const
+    {
+        uint32_t s = 0;
+        const int w0 = gather_src(Q, 0), w1 = gather_src(Q, 1);
+        for (int j = 0; j < 4; ++j) {
+            const int w = src_word(Q, j);
+            const uint32_t d = w == w0 ? (uint32_t)src_byte(Q, j)
+                                       : (w == w1 ? 4u + src_byte(Q, j) : 0u);
+            s |= d << (4 * j);
+        }
+        return s;
+    }
+    __host__ __device__ constexpr uint32_t gather_selk(int Q, int k) const
+    {
+        uint32_t s = 0;
+        const int wk = gather_src(Q, k);
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t d = src_word(Q, j) == wk ? 4u + src_byte(Q, j) : (uint32_t)j;
+            s |= d << (4 * j);
+        }
+        return s;
+    }
+};
+
+// Pairs P (pair t in the low two bits of byte t%4 of P[t/4]; the other
+// bits are ignored) into the plane bytes of a unit: per unit word one
+// byte_perm from at most two pair words and one masked merge.
+template <int CH, int PLANE, int WD = 0>
 __device__ __forceinline__ void put_unit(uint4 (&o)[CH], const uint32_t (&P)[4])
 {
-    if constexpr (T < 16) {
-        constexpr int B = T * CH + PLANE, S = 8 * (B & 3);
-        uint32_t &w = unit_word<CH, B>(o);
-        const uint32_t p = (P[T >> 2] >> (8 * (T & 3))) & 3u;
-        w = (w & ~(3u << S)) | (p << S);
-        put_unit<CH, PLANE, T + 1>(o, P);
+    if constexpr (WD < 4 * CH) {
+        constexpr UnitPlan pl{CH, PLANE};
+        constexpr uint32_t M = pl.put_mask(WD);
+        if constexpr (M != 0) {
+            constexpr int QA = pl.put_qa(WD), QB = pl.put_qb(WD);
+            constexpr uint32_t SEL = pl.put_sel(WD);
+            uint32_t &w = unit_word<CH, 4 * WD>(o);
+            const uint32_t p = __byte_perm(P[QA], P[QB], SEL);
+            w = (w & ~M) | (p & M);
+        }
+        put_unit<CH, PLANE, WD + 1>(o, P);
     }
 }
 
-// Plane-byte pairs of a unit (low two bits) into a SWAR pair array.
-template <int CH, int PLANE, int T>
-__device__ __forceinline__ void get_unit(const uint4 (&c)[CH], uint32_t (&P)[4])
+// Plane bytes of pixels 4Q..4Q+3 of a unit as one word (byte j = pixel
+// 4Q+j's whole plane byte): a chain of byte_perms over the unit words that
+// hold them.
+template <int CH, int PLANE, int Q>
+__device__ __forceinline__ uint32_t gather_word(const uint4 (&c)[CH])
+{
+    constexpr UnitPlan pl{CH, PLANE};
+    constexpr int W0 = pl.gather_src(Q, 0), W1 = pl.gather_src(Q, 1);
+    constexpr int W2 = pl.gather_src(Q, 2), W3 = pl.gather_src(Q, 3);
+    uint32_t g = __byte_perm(unit_word_c<CH, 4 * W0>(c),
+                             unit_word_c<CH, 4 * (W1 < 0 ? W0 : W1)>(c), pl.gather_sel0(Q));
+    if constexpr (W2 >= 0)
+        g = __byte_perm(g, unit_word_c<CH, 4 * W2>(c), pl.gather_selk(Q, 2));
+    if constexpr (W3 >= 0)
+        g = __byte_perm(g, unit_word_c<CH, 4 * W3>(c), pl.gather_selk(Q, 3));
+    return g;
+}
+
+// Plane bytes of a unit's 16 pixels as four words (byte t%4 of G[t/4] =
+// pixel t's plane byte).
+template <int CH, int PLANE>
+__device__ __forceinline__ void get_unit(const uint4 (&c)[CH], uint32_t (&G)[4])
+{
+    if constexpr (CH == 1) {
+        G[0] = c[0].x;
+        G[1] = c[0].y;
+        G[2] = c[0].z;
+        G[3] = c[0].w;
+    } else {
+        G[0] = gather_word<CH, PLANE, 0>(c);
+        G[1] = gather_word<CH, PLANE, 1>(c);
+        G[2] = gather_word<CH, PLANE, 2>(c);
+        G[3] = gather_word<CH, PLANE, 3>(c);
+    }
+}
+
+// Pairs of a unit's plane bytes (their low two bits) into a SWAR pair array
+// (pair t in byte t%4 of P[t/4]; P starts zeroed), one shift and mask per
+// pixel: in the extraction this measured faster than the byte_perm gather.
+template <int CH, int PLANE, int T = 0>
+__device__ __forceinline__ void get_pairs(const uint4 (&c)[CH], uint32_t (&P)[4])
 {
     if constexpr (T < 16) {
         constexpr int B = T * CH + PLANE, S = 8 * (B & 3);
-        const uint4 &v = c[B >> 4];
-        constexpr int W = (B >> 2) & 3;
-        const uint32_t w = W == 0 ? v.x : W == 1 ? v.y : W == 2 ? v.z : v.w;
+        const uint32_t w = unit_word_c<CH, B & ~3>(c);
         P[T >> 2] |= ((w >> S) & 3u) << (8 * (T & 3));
-        get_unit<CH, PLANE, T + 1>(c, P);
+        get_pairs<CH, PLANE, T + 1>(c, P);
     }
 }
 
@@ -129,7 +268,13 @@ __device__ __forceinline__ void slow_unit(uint4 (&o)[CH], uint32_t colf, uint32_
 // Four 32-bit words of message bytes mp[0..15] (mp 4-byte aligned or not).
 __device__ __forceinline__ void load16(const uint8_t *__restrict__ mp, uint32_t (&m)[4])
 {
-    if (((uintptr_t)mp & 3u) == 0) {
+    if (((uintptr_t)mp & 15u) == 0) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(mp));
+        m[0] = v.x;
+        m[1] = v.y;
+        m[2] = v.z;
+        m[3] = v.w;
+    } else if (((uintptr_t)mp & 3u) == 0) {
         const uint32_t *w = reinterpret_cast<const uint32_t *>(mp);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -142,42 +287,109 @@ __device__ __forceinline__ void load16(const uint8_t *__restrict__ mp, uint32_t 
     }
 }
 
-// Changed bytes and squared error of two vectors that differ only in the
-// low two bits of some bytes, added to 32-bit per-unit counts.
-__device__ __forceinline__ void pair_stats(const uint4 &o, const uint4 &c, uint32_t &n,
-                                           uint32_t &s)
+// Changed plane bytes and squared error of a unit from its new and old
+// plane bytes (byte t%4 of word t/4 = pixel t; only the low two bits can
+// differ, the other bits are ignored), added to 32-bit per-unit counts.
+__device__ __forceinline__ void plane_stats(const uint32_t (&Gn)[4], const uint32_t (&Go)[4],
+                                            uint32_t &n, uint32_t &s)
 {
-    const uint32_t ow[4] = {o.x, o.y, o.z, o.w}, cw[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const uint32_t x = ow[q] ^ cw[q];
-        n += __popc((x | (x >> 1)) & 0x01010101u);
-        const uint32_t d = __vabsdiffu4(ow[q] & 0x03030303u, cw[q] & 0x03030303u);
+        const uint32_t d = __vabsdiffu4(Gn[q] & 0x03030303u, Go[q] & 0x03030303u);
+        n += __popc((d | (d >> 1)) & 0x01010101u);
         s = __dp4a(d, d, s);
     }
 }
 
+// (row, unit column) advanced by dr rows and dc < upr units.
+__device__ __forceinline__ void rc_add(uint32_t &r, uint32_t &c, uint32_t dr, uint32_t dc,
+                                       uint32_t upr)
+{
+    r += dr;
+    c += dc;
+    if (c >= upr) {
+        c -= upr;
+        ++r;
+    }
+}
+
+// Units with carrying pixels, a prefix of the image's units: every unit of
+// rows 0..R-2 (4Q = W when W is a multiple of 16) and the first
+// ceil(L_last/4) of row R-1.
+__device__ __forceinline__ uint32_t carrying_units(const View &a, uint32_t upr)
+{
+    return a.R ? (a.R - 1) * upr + (a.L_last + 3) / 4 : 0u;
+}
+
+constexpr int kStageWarps = 8; // units_embed runs in CTAs of at most 256 threads
+
+// Staging slot of vector v of a warp's 32 units: CH = 4 pads one slot per 8
+// so that both the row-order and the unit-order accesses are free of bank
+// conflicts (CH = 3 is without padding).
+template <int CH>
+__device__ __forceinline__ uint32_t stage_slot(uint32_t v)
+{
+    return CH == 4 ? v + (v >> 3) : v;
+}
+
 // One pass over units k = k_first + i*step (+ u*blockDim.x, u < UT),
 // k < k_end, of an image whose rows are whole units and whose buffers are
-// 16-byte aligned.  Out of place every unit is written (units without
-// carrying pixels are copied) and each thread issues the cover loads of its
-// UT units, then their message loads, before any arithmetic.  In place
-// (INPLACE, k_end at most the units of the carrying rows) only units with
-// carrying pixels are read and written back whole.
-template <int CH, int PLANE, bool STATS, int UT, bool INPLACE = false>
+// 16-byte aligned; the lanes of a warp start at 32 consecutive units (k_first
+// = base + threadIdx.x).  STAGED with CH > 1 (CTAs of at most 256 threads),
+// the warp loads and stores its units' 32*CH vectors in memory order
+// (coalesced: a lane's own unit is 16*CH bytes apart from its neighbour's)
+// and exchanges them through shared memory, so each lane works on its own
+// unit in registers.  Every load of an iteration (cover, then
+// message) is issued before any arithmetic.  Out of place every unit is
+// written (units without carrying pixels are copied); in place (INPLACE)
+// k_end is cut to the carrying units, each vector read and written back by
+// the same lane.
+template <int CH, int PLANE, bool STATS, int UT, bool INPLACE = false, bool STAGED = true>
 __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uint32_t k_end,
                                             uint32_t step, unsigned long long &changed,
                                             unsigned long long &sse)
 {
     const uint32_t upr = a.W / 16; // units per row
-    const uint32_t carry_units = upr * a.R;
+    if (upr == 0)
+        return;
+    const uint32_t carry = carrying_units(a, upr);
+    if (INPLACE && k_end > carry)
+        k_end = carry;
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.src);
     uint4 *dst = reinterpret_cast<uint4 *>(a.dst);
-    for (uint32_t k0 = k_first; k0 < k_end; k0 += step) {
+    const uint32_t lane = threadIdx.x & 31u;
+    constexpr bool STAGE = STAGED && CH > 1;
+    constexpr uint32_t SV = 32 * CH + (CH == 4 ? 16 : 0); // slots per warp and unit group
+    __shared__ uint4 stage[STAGE ? kStageWarps * UT * SV : 1];
+    uint4 *const sw = stage + (threadIdx.x >> 5) * UT * SV;
+    const uint64_t vend = (uint64_t)k_end * CH;
+    // row and unit column of the lane's unit: with several units per thread
+    // kept by additions (the strides blockDim.x and step in whole rows and
+    // remaining units), with one unit divided out (fewer live registers)
+    constexpr bool TRACK = UT > 1;
+    uint32_t r0 = 0, u0 = 0, tr = 0, tc = 0, sr = 0, sc = 0;
+    if constexpr (TRACK) {
+        r0 = k_first / upr;
+        u0 = k_first - r0 * upr;
+        tr = blockDim.x / upr;
+        tc = blockDim.x - tr * upr;
+        sr = step / upr;
+        sc = step - sr * upr;
+    }
+    // staged, the loop runs on the warp's first unit kb (the same for every
+    // lane, so every lane runs every iteration); else on the lane's own
+    for (uint32_t k0 = k_first; (STAGE ? k0 - lane : k0) < k_end; k0 += step) {
+        const uint32_t kb = k0 - lane;
         uint4 c[UT][CH];
-        if constexpr (!INPLACE) {
 #pragma unroll
-            for (int u = 0; u < UT; ++u) {
+        for (int u = 0; u < UT; ++u) {
+            if constexpr (STAGE) { // the warp's vectors in memory order
+                const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
+#pragma unroll
+                for (int j = 0; j < CH; ++j)
+                    if (v0 + 32u * j + lane < vend)
+                        c[u][j] = __ldcs(src + v0 + 32u * j + lane);
+            } else { // the lane's own unit
                 const uint32_t k = k0 + u * blockDim.x;
                 if (k < k_end) {
 #pragma unroll
@@ -189,74 +401,108 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
         int mode[UT]; // 0: copy only, 1: one quarter (SWAR), 2: per pixel
         uint32_t colf[UT], L[UT], i0[UT], m[UT][4];
         const uint8_t *mrow[UT];
+        uint32_t r = r0, uc = u0;
 #pragma unroll
         for (int u = 0; u < UT; ++u) {
             const uint32_t k = k0 + u * blockDim.x;
+            if constexpr (TRACK) {
+                if (u > 0)
+                    rc_add(r, uc, tr, tc, upr);
+            } else {
+                r = k / upr;
+                uc = k - r * upr;
+            }
             mode[u] = 0;
-            if (k < k_end && k < carry_units) {
-                const uint32_t r = k / upr;
-                colf[u] = 16u * (k - r * upr);
+            if (k < k_end && k < carry) {
+                colf[u] = 16u * uc;
                 L[u] = row_len(a, r);
                 mrow[u] = a.msg_in + (uint64_t)r * a.Q;
-                if (colf[u] < 4 * L[u]) {
-                    i0[u] = quarter(colf[u], L[u]);
-                    if (colf[u] + 15 < 4 * L[u] && quarter(colf[u] + 15, L[u]) == i0[u]) {
-                        mode[u] = 1;
-                        load16(mrow[u] + (colf[u] - i0[u] * L[u]), m[u]);
-                    } else {
-                        mode[u] = 2;
-                    }
+                i0[u] = quarter(colf[u], L[u]);
+                if (colf[u] + 15 < 4 * L[u] && quarter(colf[u] + 15, L[u]) == i0[u]) {
+                    mode[u] = 1;
+                    load16(mrow[u] + (colf[u] - i0[u] * L[u]), m[u]);
+                } else {
+                    mode[u] = 2;
                 }
             }
         }
-        if constexpr (INPLACE) {
+        if constexpr (STAGE) {
+            __syncwarp(); // the previous iteration's stores have read their slots
 #pragma unroll
             for (int u = 0; u < UT; ++u) {
-                if (mode[u]) {
-                    const uint32_t k = k0 + u * blockDim.x;
+                const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
+#pragma unroll
+                for (int j = 0; j < CH; ++j)
+                    if (v0 + 32u * j + lane < vend)
+                        sw[u * SV + stage_slot<CH>(32u * j + lane)] = c[u][j];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < UT; ++u) {
+                if (k0 + u * blockDim.x < k_end) {
 #pragma unroll
                     for (int q = 0; q < CH; ++q)
-                        c[u][q] = __ldcs(src + (uint64_t)k * CH + q);
+                        c[u][q] = sw[u * SV + stage_slot<CH>(CH * lane + q)];
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < UT; ++u) {
             const uint32_t k = k0 + u * blockDim.x;
-            if (k >= k_end || (INPLACE && !mode[u]))
+            if (k >= k_end)
                 continue;
-            uint4 o[CH];
-#pragma unroll
-            for (int q = 0; q < CH; ++q)
-                o[q] = c[u][q];
+            uint4(&o)[CH] = c[u]; // rewritten in registers
+            uint32_t Gn[4], Go[4];
+            if (STATS && mode[u])
+                get_unit<CH, PLANE>(o, Go); // old plane bytes
             if (mode[u] == 1) {
-                uint32_t P[4];
+                // pair of quarter i0 in the low two bits of each byte
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    P[q] = (m[u][q] >> (2 * i0[u])) & 0x03030303u;
-                if (CH == 1) {
-                    o[0].x = (o[0].x & 0xFCFCFCFCu) | P[0];
-                    o[0].y = (o[0].y & 0xFCFCFCFCu) | P[1];
-                    o[0].z = (o[0].z & 0xFCFCFCFCu) | P[2];
-                    o[0].w = (o[0].w & 0xFCFCFCFCu) | P[3];
+                    Gn[q] = m[u][q] >> (2 * i0[u]);
+                if constexpr (CH == 1) {
+                    o[0].x = (o[0].x & 0xFCFCFCFCu) | (Gn[0] & 0x03030303u);
+                    o[0].y = (o[0].y & 0xFCFCFCFCu) | (Gn[1] & 0x03030303u);
+                    o[0].z = (o[0].z & 0xFCFCFCFCu) | (Gn[2] & 0x03030303u);
+                    o[0].w = (o[0].w & 0xFCFCFCFCu) | (Gn[3] & 0x03030303u);
                 } else {
-                    put_unit<CH, PLANE, 0>(o, P);
+                    put_unit<CH, PLANE>(o, Gn);
                 }
             } else if (mode[u] == 2) {
                 slow_unit<CH, PLANE, 0>(o, colf[u], L[u], mrow[u]);
+                if (STATS)
+                    get_unit<CH, PLANE>(o, Gn);
             }
             if (STATS && mode[u]) {
                 uint32_t n = 0, sq = 0; // at most 16 pairs changed, 9 each
-#pragma unroll
-                for (int q = 0; q < CH; ++q)
-                    pair_stats(o[q], c[u][q], n, sq);
+                plane_stats(Gn, Go, n, sq);
                 changed += n;
                 sse += sq;
             }
+            if constexpr (STAGE) {
 #pragma unroll
-            for (int q = 0; q < CH; ++q)
-                __stcs(dst + (uint64_t)k * CH + q, o[q]);
+                for (int q = 0; q < CH; ++q)
+                    sw[u * SV + stage_slot<CH>(CH * lane + q)] = o[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < CH; ++q)
+                    __stcs(dst + (uint64_t)k * CH + q, o[q]);
+            }
         }
+        if constexpr (STAGE) {
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < UT; ++u) {
+                const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
+#pragma unroll
+                for (int j = 0; j < CH; ++j)
+                    if (v0 + 32u * j + lane < vend)
+                        __stcs(dst + v0 + 32u * j + lane,
+                               sw[u * SV + stage_slot<CH>(32u * j + lane)]);
+            }
+        }
+        if constexpr (TRACK)
+            rc_add(r0, u0, sr, sc, upr);
     }
 }
 
@@ -373,13 +619,13 @@ __device__ __forceinline__ void runs_extract(const View &a, uint64_t k_first, ui
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 uint32_t P[4] = {0u, 0u, 0u, 0u};
-                if (CH == 1) {
+                if constexpr (CH == 1) {
                     P[0] = c[i][0].x & 0x03030303u;
                     P[1] = c[i][0].y & 0x03030303u;
                     P[2] = c[i][0].z & 0x03030303u;
                     P[3] = c[i][0].w & 0x03030303u;
                 } else {
-                    get_unit<CH, PLANE, 0>(c[i], P);
+                    get_pairs<CH, PLANE>(c[i], P);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q)

@@ -42,13 +42,15 @@ __device__ __forceinline__ void write_res(const P2Args &a, bool stats)
     }
 }
 
-constexpr int kUnitThreads = 256; // p2_embed_units' register bound assumes it
+constexpr int kUnitThreads = 256; // at most 256: the staging area holds 8 warps
 constexpr int kUnitsPerThread = 2;
 
-// Out of place every unit of the image; in place the units of the carrying
-// rows (those without carrying pixels are skipped).
+// Out of place every unit of the image; in place the units with carrying
+// pixels.  Two CTAs per SM: the staged units take 107-112 registers, and
+// capped at 80 for three CTAs they spilled and ran slower (8192x8192x3,
+// plane 0: 70-72 against 67.6 us).
 template <int CH, int PLANE, bool STATS, bool INPLACE>
-__global__ void __launch_bounds__(kUnitThreads, 3) p2_embed_units(P2Args a)
+__global__ void __launch_bounds__(kUnitThreads, 2) p2_embed_units(P2Args a)
 {
     unsigned long long changed = 0, sse = 0;
     write_res(a, STATS);
