@@ -233,4 +233,24 @@ __device__ __forceinline__ void word_stats(uint32_t x, uint32_t y, unsigned long
     sse += __dp4a(a, a, 0u);
 }
 
+// Warp staging of pixel units (16 pixels of CH channels = CH 16-byte
+// vectors): a warp's 32 consecutive units are loaded and stored in memory
+// order and exchanged through shared memory, SV = unit_stage_slots<CH>()
+// slots per warp.  Vector v of the warp's units sits in slot
+// unit_stage_slot<CH>(v); CH = 4 pads one slot per 8 so that both the
+// memory-order (v = 32j + lane) and the unit-order (v = CH*lane + q)
+// accesses are free of bank conflicts (CH = 3 needs no padding).
+template <int CH>
+__host__ __device__ constexpr uint32_t unit_stage_slots()
+{
+    return 32 * CH + (CH == 4 ? 16 : 0);
+}
+
+template <int CH>
+__device__ __forceinline__ uint32_t unit_stage_slot(uint32_t v)
+{
+    return CH == 4 ? v + (v >> 3) : v;
+}
+
 } // namespace stego
+

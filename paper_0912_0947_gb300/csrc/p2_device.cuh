@@ -323,15 +323,6 @@ __device__ __forceinline__ uint32_t carrying_units(const View &a, uint32_t upr)
 
 constexpr int kStageWarps = 8; // units_embed runs in CTAs of at most 256 threads
 
-// Staging slot of vector v of a warp's 32 units: CH = 4 pads one slot per 8
-// so that both the row-order and the unit-order accesses are free of bank
-// conflicts (CH = 3 is without padding).
-template <int CH>
-__device__ __forceinline__ uint32_t stage_slot(uint32_t v)
-{
-    return CH == 4 ? v + (v >> 3) : v;
-}
-
 // One pass over units k = k_first + i*step (+ u*blockDim.x, u < UT),
 // k < k_end, of an image whose rows are whole units and whose buffers are
 // 16-byte aligned; the lanes of a warp start at 32 consecutive units (k_first
@@ -359,7 +350,7 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
     uint4 *dst = reinterpret_cast<uint4 *>(a.dst);
     const uint32_t lane = threadIdx.x & 31u;
     constexpr bool STAGE = STAGED && CH > 1;
-    constexpr uint32_t SV = 32 * CH + (CH == 4 ? 16 : 0); // slots per warp and unit group
+    constexpr uint32_t SV = unit_stage_slots<CH>(); // slots per warp and unit group
     __shared__ uint4 stage[STAGE ? kStageWarps * UT * SV : 1];
     uint4 *const sw = stage + (threadIdx.x >> 5) * UT * SV;
     const uint64_t vend = (uint64_t)k_end * CH;
@@ -434,7 +425,7 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
 #pragma unroll
                 for (int j = 0; j < CH; ++j)
                     if (v0 + 32u * j + lane < vend)
-                        sw[u * SV + stage_slot<CH>(32u * j + lane)] = c[u][j];
+                        sw[u * SV + unit_stage_slot<CH>(32u * j + lane)] = c[u][j];
             }
             __syncwarp();
 #pragma unroll
@@ -442,7 +433,7 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
                 if (k0 + u * blockDim.x < k_end) {
 #pragma unroll
                     for (int q = 0; q < CH; ++q)
-                        c[u][q] = sw[u * SV + stage_slot<CH>(CH * lane + q)];
+                        c[u][q] = sw[u * SV + unit_stage_slot<CH>(CH * lane + q)];
                 }
             }
         }
@@ -482,7 +473,7 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
             if constexpr (STAGE) {
 #pragma unroll
                 for (int q = 0; q < CH; ++q)
-                    sw[u * SV + stage_slot<CH>(CH * lane + q)] = o[q];
+                    sw[u * SV + unit_stage_slot<CH>(CH * lane + q)] = o[q];
             } else {
 #pragma unroll
                 for (int q = 0; q < CH; ++q)
@@ -498,7 +489,7 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
                 for (int j = 0; j < CH; ++j)
                     if (v0 + 32u * j + lane < vend)
                         __stcs(dst + v0 + 32u * j + lane,
-                               sw[u * SV + stage_slot<CH>(32u * j + lane)]);
+                               sw[u * SV + unit_stage_slot<CH>(32u * j + lane)]);
             }
         }
         if constexpr (TRACK)
