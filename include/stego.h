@@ -203,9 +203,10 @@ int stego_capacity(uint64_t cover_bytes, const stego_geom *geom, uint32_t flags,
 /* Embed (Section VI).  Writes cover_bytes bytes of d_stego (out of place) or,
  * in place, the T = 8*|S| carrying bytes (STREAM1) / the 4*msg_bytes plane
  * bytes (PAPER2; with 1, 3 or 4 channels, rows of whole 16-byte vectors and
- * a 16-byte aligned buffer the 16-pixel groups of the carrying rows are
- * rewritten whole, the bytes outside the plane's carrying bytes with their
- * own values).  Bytes that do not carry the message keep their values.
+ * a 16-byte aligned buffer whole 16-pixel groups are rewritten, the bytes
+ * outside the plane's carrying bytes with their own values: those groups
+ * holding carrying pixels, in a batched call every group of the carrying
+ * rows).  Bytes that do not carry the message keep their values.
  *   d_cover, d_stego  cover and output image, cover_bytes each.
  *   d_msg, msg_bytes  message (may be NULL when msg_bytes == 0).
  *   geom              PAPER2 geometry (host pointer) or NULL for STREAM1.

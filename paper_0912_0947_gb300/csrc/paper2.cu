@@ -4,9 +4,9 @@
 // per-row routines live in p2_device.cuh and are shared with the batched
 // kernels.
 //   p2_embed_units<CH,PLANE,STATS,INPLACE>  persistent grid over 16-pixel
-//       units; 256-thread CTAs, 3 per SM.  Out of place one pass (2C + N
-//       bytes); in place the units of the carrying rows, read and written
-//       back whole.
+//       units; 256-thread CTAs, 2 per SM, each warp's units staged through
+//       shared memory.  Out of place one pass (2C + N bytes); in place the
+//       units with carrying pixels, read and written back whole.
 //   p2_embed_rows  the scatter after a copy (and in place) for layouts the
 //       unit kernel does not take; CTAs stride over carrying rows.
 //   p2_extract_units<CH,PLANE>  runs of 16 message bytes (CH in {1,3,4}).
@@ -190,8 +190,8 @@ cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
     P2Args a = make_args(cover, stego, g, msg, nullptr, N, res);
     a.slot = stats ? slot : nullptr;
     if (cover == stego && units_layout_ok(stego, g)) {
-        // in place over the units of the carrying rows: whole vectors
-        // instead of one byte access per plane byte
+        // in place over the units with carrying pixels (cut inside the
+        // kernel): whole vectors instead of one byte access per plane byte
         const void *k = stats ? units_kernel<true, true>(g.channels, g.plane)
                               : units_kernel<false, true>(g.channels, g.plane);
         const uint64_t nunits = (uint64_t)(g.width / 16u) * a.v.R;
