@@ -144,6 +144,24 @@ int sm_count()
     return n;
 }
 
+cudaError_t launch_dependent(const void *kernel, dim3 grid, dim3 block, void **args,
+                             size_t smem, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    std::memset(at, 0, sizeof(at));
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
 int persistent_grid(const void *kernel, int threads, size_t smem, int ctas_per_sm,
                     uint64_t units, uint64_t units_per_cta)
 {

@@ -17,6 +17,8 @@ constexpr int kWordsPerWarp = 4; // message words per warp per iteration, loads 
 
 __global__ void __launch_bounds__(512) extract_ballot(s1::ExtractArgs a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     s1::ExtractView x;
     if (s1::extract_prologue(a, x) != STEGO_OK)
         return;
@@ -86,7 +88,7 @@ cudaError_t s1_extract_ballot(const uint8_t *st, uint64_t C, uint8_t *msg, uint6
     const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, words ? words : 1,
                                      (uint64_t)(T / 32) * kWordsPerWarp);
     void *args[] = {&a};
-    return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
 }
 
 } // namespace stego

@@ -141,6 +141,8 @@ __device__ __forceinline__ uint64_t rows_for(const stego_desc &D, uint32_t tile_
 __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *results, WsView ws,
                            uint32_t tile_bytes)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
         const stego_desc D = descs[d];
         const uint32_t layout = D.flags & STEGO_LAYOUT_MASK;
@@ -236,6 +238,8 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
 __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *results,
                              WsView ws, uint32_t tile_bytes)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
         const stego_desc D = descs[d];
         const uint32_t layout = D.flags & STEGO_LAYOUT_MASK;
@@ -362,6 +366,8 @@ __device__ __forceinline__ unsigned long long scan_one(unsigned long long *count
 
 __global__ void __launch_bounds__(kScanThreads) scan_tiles(WsView ws, uint32_t n)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     __shared__ unsigned long long part[kScanThreads];
     const unsigned long long ts = scan_one(ws.start, n, part);
     const unsigned long long tp = scan_one(ws.start_p, n, part);
@@ -496,6 +502,8 @@ __global__ void __launch_bounds__(512) persist_embed(const stego_desc *descs, ui
                                                      stego_result *results, WsView ws,
                                                      uint32_t tile_bytes)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     uint32_t stat_d = 0xFFFFFFFFu;
     claim_loop(ws.start, ws.head->total, &ws.head->counter, n,
@@ -537,6 +545,8 @@ template <int V>
 __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, uint32_t n,
                                                        WsView ws, uint32_t tile_bytes)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     claim_loop(ws.start, ws.head->total, &ws.head->counter, n,
                [&](uint32_t d, unsigned long long lt) {
         const stego_desc &D = descs[d];
@@ -569,6 +579,8 @@ template <bool STATS>
 __global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *descs, uint32_t n,
                                                         stego_result *results, WsView ws)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     uint32_t stat_d = 0xFFFFFFFFu;
     claim_loop(ws.start_p, ws.head->total_p, &ws.head->counter_p, n,
@@ -586,6 +598,8 @@ __global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *des
 __global__ void __launch_bounds__(256, 3) persist_p2_extract(const stego_desc *descs, uint32_t n,
                                                           WsView ws)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     claim_loop(ws.start_p, ws.head->total_p, &ws.head->counter_p, n,
                [&](uint32_t d, unsigned long long lt) {
         paper_extract_tile(descs[d], ws.info[d], lt);
@@ -641,27 +655,32 @@ int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint
     const int prep_cap = sm_count() * 8;
     if (prep_grid > prep_cap)
         prep_grid = prep_cap;
-    if (EMBED)
-        prep_embed<<<prep_grid, prep_threads, 0, s>>>(d_descs, n, d_results, ws, tile);
-    else
-        prep_extract<<<prep_grid, prep_threads, 0, s>>>(d_descs, n, d_results, ws, tile);
-    if (cudaGetLastError() != cudaSuccess)
+    cudaError_t e;
+    {
+        uint32_t tile_arg = tile;
+        void *args[] = {(void *)&d_descs, &n, &d_results, &ws, &tile_arg};
+        e = launch_dependent(EMBED ? (const void *)prep_embed : (const void *)prep_extract,
+                             dim3(prep_grid), dim3(prep_threads), args, 0, s);
+    }
+    if (e != cudaSuccess)
         return STEGO_E_CUDA;
-    scan_tiles<<<1, kScanThreads, 0, s>>>(ws, n);
-    if (cudaGetLastError() != cudaSuccess)
+    {
+        void *args[] = {&ws, &n};
+        e = launch_dependent((const void *)scan_tiles, dim3(1), dim3(kScanThreads), args, 0, s);
+    }
+    if (e != cudaSuccess)
         return STEGO_E_CUDA;
 
     const bool stats = (flags & STEGO_FUSE_STATS) != 0;
     const void *k = persist_kernel<EMBED>(sh.vec, stats);
     // the tile count lives on the device: launch the full persistent grid
     const int grid = persistent_grid(k, sh.threads, 0, sh.ctas_per_sm, ~0ull >> 1, 1);
-    cudaError_t e;
     if (EMBED) {
         void *args[] = {(void *)&d_descs, &n, &d_results, &ws, (void *)&tile};
-        e = cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+        e = launch_dependent(k, dim3(grid), dim3(sh.threads), args, 0, s);
     } else {
         void *args[] = {(void *)&d_descs, &n, &ws, (void *)&tile};
-        e = cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+        e = launch_dependent(k, dim3(grid), dim3(sh.threads), args, 0, s);
     }
     if (e != cudaSuccess)
         return STEGO_E_CUDA;
@@ -673,10 +692,10 @@ int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint
     const int gridp = persistent_grid(kp, p2_threads, 0, 0, ~0ull >> 1, 1);
     if (EMBED) {
         void *args[] = {(void *)&d_descs, &n, &d_results, &ws};
-        e = cudaLaunchKernel(kp, dim3(gridp), dim3(p2_threads), args, 0, s);
+        e = launch_dependent(kp, dim3(gridp), dim3(p2_threads), args, 0, s);
     } else {
         void *args[] = {(void *)&d_descs, &n, &ws};
-        e = cudaLaunchKernel(kp, dim3(gridp), dim3(p2_threads), args, 0, s);
+        e = launch_dependent(kp, dim3(gridp), dim3(p2_threads), args, 0, s);
     }
     return e == cudaSuccess ? STEGO_OK : STEGO_E_CUDA;
 }

@@ -241,6 +241,8 @@ __device__ __forceinline__ void tile_pairs(const s1::EmbedView &a, const Ring &r
 template <int V, bool STATS>
 __global__ void __launch_bounds__(512) embed_bulk(BulkEmbedArgs e)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     extern __shared__ __align__(128) uint8_t ring_mem[];
     __shared__ __align__(8) uint64_t full[kMaxStages];
     const s1::EmbedView &a = e.a;
@@ -356,6 +358,8 @@ struct BulkExtractArgs {
 template <int V>
 __global__ void __launch_bounds__(512) extract_bulk(BulkExtractArgs e)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     extern __shared__ __align__(128) uint8_t ring_mem[];
     __shared__ __align__(8) uint64_t full[kMaxStages];
     s1::ExtractView x;
@@ -514,7 +518,7 @@ cudaError_t s1_embed_bulk(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes
     const uint64_t ntiles = ((n_bytes >> 4) + tvec - 1) / tvec;
     const int grid = persistent_grid(k, sh.threads, ring, sh.ctas_per_sm, ntiles ? ntiles : 1, 1);
     void *args[] = {&e};
-    return cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, ring, s);
+    return launch_dependent(k, dim3(grid), dim3(sh.threads), args, ring, s);
 }
 
 cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
@@ -548,7 +552,7 @@ cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_
     const uint64_t ntiles = ((max_len >> 1) + tvec - 1) / tvec;
     const int grid = persistent_grid(k, sh.threads, ring, sh.ctas_per_sm, ntiles ? ntiles : 1, 1);
     void *args[] = {&e};
-    return cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, ring, s);
+    return launch_dependent(k, dim3(grid), dim3(sh.threads), args, ring, s);
 }
 
 } // namespace stego

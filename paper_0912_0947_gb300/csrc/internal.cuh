@@ -37,6 +37,29 @@ int sm_count();
 int persistent_grid(const void *kernel, int threads, size_t smem, int ctas_per_sm,
                     uint64_t units, uint64_t units_per_cta);
 
+// Programmatic dependent launch: the kernel may be launched while the kernel
+// before it in the stream is still finishing (its CTAs then wait on the SMs
+// instead of behind the launch).  Only for kernels that call
+// grid_dependency_wait() before their first global memory access.
+cudaError_t launch_dependent(const void *kernel, dim3 grid, dim3 block, void **args,
+                             size_t smem, cudaStream_t s);
+
+// Returns once the grid before this one in the stream has completed and its
+// memory operations are visible (at once when there is none, or when the
+// launch was an ordinary one).
+__device__ __forceinline__ void grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Lets the next kernel in the stream that was launched with
+// launch_dependent start launching (it still waits for this grid's end in
+// its own grid_dependency_wait()).
+__device__ __forceinline__ void allow_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Fused statistics without a zeroing copy
 // ---------------------------------------------------------------------------

@@ -52,6 +52,8 @@ constexpr int kUnitsPerThread = 2;
 template <int CH, int PLANE, bool STATS, bool INPLACE>
 __global__ void __launch_bounds__(kUnitThreads, 2) p2_embed_units(P2Args a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     write_res(a, STATS);
     const uint32_t nunits = a.v.W / 16 * (INPLACE ? a.v.R : a.v.H);
@@ -65,6 +67,8 @@ __global__ void __launch_bounds__(kUnitThreads, 2) p2_embed_units(P2Args a)
 template <bool STATS>
 __global__ void __launch_bounds__(512, 2) p2_embed_rows(P2Args a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     write_res(a, STATS);
     p2::rows_embed<STATS>(a.v, blockIdx.x, a.v.R, gridDim.x, changed, sse);
@@ -86,6 +90,8 @@ __device__ __forceinline__ void extract_res(const P2Args &a)
 template <int CH, int PLANE>
 __global__ void __launch_bounds__(512) p2_extract_units(P2Args a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     extract_res(a);
     const uint64_t nruns = (uint64_t)((a.v.Q + 15) / 16) * a.v.R;
     p2::runs_extract<CH, PLANE>(a.v, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nruns,
@@ -94,6 +100,8 @@ __global__ void __launch_bounds__(512) p2_extract_units(P2Args a)
 
 __global__ void __launch_bounds__(512) p2_extract_rows(P2Args a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     extract_res(a);
     p2::rows_extract(a.v, blockIdx.x, a.v.R, gridDim.x);
 }
@@ -180,7 +188,7 @@ cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geo
     const int grid = persistent_grid(k, kUnitThreads, 0, kAnyCtas, nunits ? nunits : 1,
                                      (uint64_t)kUnitThreads * kUnitsPerThread);
     void *args[] = {&a};
-    return cudaLaunchKernel(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
 }
 
 cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
@@ -199,12 +207,12 @@ cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
                                          nunits ? nunits : 1,
                                          (uint64_t)kUnitThreads * kUnitsPerThread);
         void *args[] = {&a};
-        return cudaLaunchKernel(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
+        return launch_dependent(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
     }
     const void *k = stats ? (const void *)p2_embed_rows<true> : (const void *)p2_embed_rows<false>;
     const int grid = row_grid(k, sh, a.v.R);
     void *args[] = {&a};
-    return cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(sh.threads), args, 0, s);
 }
 
 cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uint64_t N,
@@ -217,11 +225,11 @@ cudaError_t p2_extract(const uint8_t *st, const stego_geom &g, uint8_t *msg, uin
         const uint64_t runs = (uint64_t)((a.v.Q + 15) / 16) * a.v.R;
         const int grid = persistent_grid(k, sh.threads, 0, kAnyCtas, runs ? runs : 1,
                                          (uint64_t)sh.threads);
-        return cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+        return launch_dependent(k, dim3(grid), dim3(sh.threads), args, 0, s);
     }
     const void *k = (const void *)p2_extract_rows;
     const int grid = row_grid(k, sh, a.v.R);
-    return cudaLaunchKernel(k, dim3(grid), dim3(sh.threads), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(sh.threads), args, 0, s);
 }
 
 } // namespace stego

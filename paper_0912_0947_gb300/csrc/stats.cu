@@ -16,6 +16,8 @@ __global__ void __launch_bounds__(512) changed_vec(const uint4 *__restrict__ a,
                                                     const uint8_t *a8, const uint8_t *b8,
                                                     uint64_t n, unsigned long long *out)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * V;
     for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x; v0 < nvec;
@@ -53,6 +55,8 @@ __global__ void __launch_bounds__(512) changed_vec(const uint4 *__restrict__ a,
 __global__ void __launch_bounds__(512) changed_bytes_kernel(const uint8_t *a, const uint8_t *b,
                                                              uint64_t n, unsigned long long *out)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (uint64_t)gridDim.x * blockDim.x) {
@@ -85,12 +89,12 @@ cudaError_t changed_bytes(const uint8_t *a, const uint8_t *b, uint64_t n,
         const uint4 *av = reinterpret_cast<const uint4 *>(a);
         const uint4 *bv = reinterpret_cast<const uint4 *>(b);
         void *args[] = {&av, &bv, (void *)&nvec, &a, &b, &n, &out2};
-        return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+        return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
     }
     const void *k = (const void *)changed_bytes_kernel;
     const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, n > 0 ? n : 1, (uint64_t)T * 16);
     void *args[] = {&a, &b, &n, &out2};
-    return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
 }
 
 } // namespace stego

@@ -50,6 +50,8 @@ __device__ __forceinline__ void write_res(const EmbedArgs &e, bool stats)
 template <int V, bool STATS>
 __global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     write_res(e, STATS);
     const uint64_t nvec = e.a.n_bytes >> 4;
@@ -71,6 +73,8 @@ __global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
 template <int V, bool STATS>
 __global__ void __launch_bounds__(512) embed_shift(EmbedArgs e, uint32_t h)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     write_res(e, STATS);
     const uint64_t nvb = (e.a.n_bytes - h) >> 4;
@@ -94,6 +98,8 @@ __global__ void __launch_bounds__(512) embed_shift(EmbedArgs e, uint32_t h)
 template <bool STATS>
 __global__ void __launch_bounds__(512) embed_bytes(EmbedArgs e)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     write_res(e, STATS);
     s1::embed_bytes_range<STATS>(e.a, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
@@ -114,6 +120,8 @@ using s1::extract_prologue;
 template <int V>
 __global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x;
     const uint64_t round = (uint64_t)gridDim.x * blockDim.x * V;
     const uint4 *__restrict__ src =
@@ -156,6 +164,8 @@ __global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
 template <int V>
 __global__ void __launch_bounds__(512) extract_shift(ExtractArgs a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     ExtractView x;
     if (extract_prologue(a, x) != STEGO_OK)
         return;
@@ -211,7 +221,7 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
         const uint64_t nvec = n_bytes >> 4;
         const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvec > 0 ? nvec : 1,
                                          (uint64_t)T * vec);
-        return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+        return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
     }
     const uint32_t h = (uint32_t)((16u - ((uintptr_t)cover & 15u)) & 15u);
     if ((((uintptr_t)cover ^ (uintptr_t)stego) & 15u) == 0 && n_bytes >= (uint64_t)h + 16u) {
@@ -220,12 +230,12 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
         const uint64_t nvb = (n_bytes - h) >> 4;
         const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvb, (uint64_t)T * kShiftV);
         void *sargs[] = {&e, (void *)&h};
-        return cudaLaunchKernel(k, dim3(grid), dim3(T), sargs, 0, s);
+        return launch_dependent(k, dim3(grid), dim3(T), sargs, 0, s);
     }
     const void *k = stats ? (const void *)embed_bytes<true> : (const void *)embed_bytes<false>;
     const uint64_t units = (n_bytes + 7) >> 3;
     const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, units > 0 ? units : 1, (uint64_t)T);
-    return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
 }
 
 cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap,
@@ -264,13 +274,13 @@ cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap
         const uint64_t nvec = max_len >> 1;
         const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvec > 0 ? nvec : 1,
                                          (uint64_t)T * vec);
-        return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+        return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
     }
     const void *k = (const void *)extract_shift<kShiftV>;
     const uint64_t npairs = max_len >> 1;
     const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, npairs > 0 ? npairs : 1,
                                      (uint64_t)T * kShiftV);
-    return cudaLaunchKernel(k, dim3(grid), dim3(T), args, 0, s);
+    return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
 }
 
 } // namespace stego

@@ -361,6 +361,8 @@ __host__ __device__ constexpr int units_per_iter()
 template <int K, int CH, int PLANE, bool STATS>
 __global__ void __launch_bounds__(512) embedk_units(KView a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     constexpr int U = units_per_iter<CH, true>();
     constexpr uint32_t MASK = (1u << K) - 1u;
     constexpr uint32_t BYTEMASK = MASK * 0x01010101u;
@@ -439,6 +441,8 @@ __global__ void __launch_bounds__(512) embedk_units(KView a)
 template <bool STATS>
 __global__ void __launch_bounds__(512) embedk_bytes(KView a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     unsigned long long changed = 0, sse = 0;
     embed_res(a, STATS);
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.n_carry;
@@ -513,6 +517,8 @@ __device__ __forceinline__ int extractk_prologue(const KView &a, uint64_t &len)
 template <int K, int CH, int PLANE>
 __global__ void __launch_bounds__(512) extractk_units(KView a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     uint64_t len;
     if (extractk_prologue(a, len) != STEGO_OK)
         return;
@@ -578,6 +584,8 @@ __global__ void __launch_bounds__(512) extractk_units(KView a)
 // Any alignment, any k, either carrying order: one thread per message byte.
 __global__ void __launch_bounds__(512) extractk_bytes(KView a)
 {
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
     uint64_t len;
     if (extractk_prologue(a, len) != STEGO_OK)
         return;
@@ -714,7 +722,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
         const int per_thread = a.channels == 1 ? kEmbedAllBytesUnits : 1;
         const int grid = persistent_grid(kern, T, 0, kAnyCtas, nunits ? nunits : 1,
                                          (uint64_t)T * per_thread);
-        return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
+        return launch_dependent(kern, dim3(grid), dim3(T), args, 0, s);
     }
     if (plane_only && !inplace) {
         // the non-carrying bytes come from a copy of the cover (a stream
@@ -727,7 +735,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     const void *kern = stats ? (const void *)embedk_bytes<true> : (const void *)embedk_bytes<false>;
     const int grid = persistent_grid(kern, T, 0, kAnyCtas, a.n_carry ? a.n_carry : 1,
                                      (uint64_t)T * 16);
-    return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
+    return launch_dependent(kern, dim3(grid), dim3(T), args, 0, s);
 }
 
 cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_only,
@@ -762,11 +770,11 @@ cudaError_t sk_extract(const uint8_t *st, uint64_t C, uint32_t k, bool plane_onl
         const int per_thread = a.channels == 1 ? kExtractAllBytesUnits : 1;
         const int grid = persistent_grid(kern, T, 0, kAnyCtas, nunits ? nunits : 1,
                                          (uint64_t)T * per_thread);
-        return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
+        return launch_dependent(kern, dim3(grid), dim3(T), args, 0, s);
     }
     const void *kern = (const void *)extractk_bytes;
     const int grid = persistent_grid(kern, T, 0, kAnyCtas, max_len ? max_len : 1, (uint64_t)T);
-    return cudaLaunchKernel(kern, dim3(grid), dim3(T), args, 0, s);
+    return launch_dependent(kern, dim3(grid), dim3(T), args, 0, s);
 }
 
 } // namespace stego
