@@ -287,6 +287,58 @@ __device__ __forceinline__ void embed_shift_range(const EmbedView &a, uint32_t h
     }
 }
 
+// 16 bytes starting at byte 4Q + b of the 32 bytes lo:hi (lo first);
+// sel = b | (b+1) << 4 | (b+2) << 8 | (b+3) << 12 selects them per word.
+template <int Q>
+__device__ __forceinline__ uint4 funnel16(const uint4 &lo, const uint4 &hi, uint32_t sel)
+{
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    return make_uint4(__byte_perm(w[Q], w[Q + 1], sel), __byte_perm(w[Q + 1], w[Q + 2], sel),
+                      __byte_perm(w[Q + 2], w[Q + 3], sel), __byte_perm(w[Q + 3], w[Q + 4], sel));
+}
+
+// Cover and stego at different addresses mod 16 (out of place, n_bytes =
+// C): h = (-stego) mod 16 head bytes, then aligned stego vectors j at stego
+// + h + 16j (j < j_end).  The cover bytes of vector j, h + 16j .. h + 16j +
+// 15, start at byte d = (cover + h) mod 16 = 4Q + (sel's b) of the aligned
+// cover vector at or below them: they come from that vector and the next,
+// each loaded whole, joined by funnel16.  A vector whose two cover vectors
+// are not both inside the cover reads its 16 cover bytes one by one.  Head
+// and tail bytes are left to the caller.
+template <int Q, bool STATS>
+__device__ __forceinline__ void embed_funnel_range(const EmbedView &a, uint32_t h, uint32_t sel,
+                                                   uint64_t j_first, uint64_t j_end,
+                                                   uint64_t step, unsigned long long &changed,
+                                                   unsigned long long &sse)
+{
+    const uintptr_t c0 = (uintptr_t)(a.cover + h);
+    const uint4 *__restrict__ A = reinterpret_cast<const uint4 *>(c0 & ~(uintptr_t)15u);
+    const uintptr_t lo_ok = (uintptr_t)a.cover, hi_ok = (uintptr_t)a.cover + a.n_bytes;
+    uint4 *dst = reinterpret_cast<uint4 *>(a.stego + h);
+    uint32_t n = 0;
+    for (uint64_t j = j_first; j < j_end; j += step) {
+        const uintptr_t b = (uintptr_t)(A + j);
+        const uint64_t k0 = h + (j << 4);
+        uint4 c;
+        if (b >= lo_ok && b + 32u <= hi_ok) {
+            const uint4 lo = __ldcs(A + j), hi = __ldcs(A + j + 1);
+            c = funnel16<Q>(lo, hi, sel);
+        } else {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                w[t >> 2] |= (uint32_t)a.cover[k0 + t] << (8 * (t & 3));
+            c = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        const uint32_t p = k0 < a.t_bytes ? stream_bits16(a, k0) : 0u;
+        __stcs(dst + j, embed_vec16_at<STATS>(a, k0, c, p, n));
+    }
+    if (STATS) {
+        changed += n;
+        sse += n;
+    }
+}
+
 // One byte k of a job (tails and unaligned buffers).
 template <bool STATS>
 __device__ __forceinline__ void embed_one(const EmbedView &a, uint64_t k, uint32_t s,

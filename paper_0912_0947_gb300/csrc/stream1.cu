@@ -67,6 +67,21 @@ __global__ void __launch_bounds__(512) embed_vec(EmbedArgs e)
         block_stats(changed, sse, e.res, e.slot);
 }
 
+// The h head bytes and the bytes after the nvb aligned vectors that follow
+// them (fewer than 32 in all), one per thread of the calling CTA.
+template <bool STATS>
+__device__ __forceinline__ void head_tail(const s1::EmbedView &a, uint32_t h, uint64_t nvb,
+                                          unsigned long long &changed, unsigned long long &sse)
+{
+    const uint32_t tail = (uint32_t)(a.n_bytes - h - (nvb << 4));
+    if (threadIdx.x < h + tail) {
+        const uint64_t k = threadIdx.x < h ? (uint64_t)threadIdx.x
+                                           : h + (nvb << 4) + (threadIdx.x - h);
+        const uint32_t sb = k < a.t_bytes ? s1::stream_byte(a, k >> 3) : 0u;
+        s1::embed_one<STATS>(a, k, sb, changed, sse);
+    }
+}
+
 // Cover and stego with the same misalignment: aligned vectors after h head
 // bytes, the stream cut at bit h % 8; block 0 does the head and the tail
 // (fewer than 32 bytes).  Requires n_bytes >= h.
@@ -80,15 +95,28 @@ __global__ void __launch_bounds__(512) embed_shift(EmbedArgs e, uint32_t h)
     const uint64_t nvb = (e.a.n_bytes - h) >> 4;
     s1::embed_shift_range<V, STATS>(e.a, h, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x,
                                     nvb, (uint64_t)gridDim.x * blockDim.x * V, changed, sse);
-    if (blockIdx.x == 0) {
-        const uint32_t tail = (uint32_t)(e.a.n_bytes - h - (nvb << 4));
-        if (threadIdx.x < h + tail) {
-            const uint64_t k = threadIdx.x < h ? (uint64_t)threadIdx.x
-                                               : h + (nvb << 4) + (threadIdx.x - h);
-            const uint32_t sb = k < e.a.t_bytes ? s1::stream_byte(e.a, k >> 3) : 0u;
-            s1::embed_one<STATS>(e.a, k, sb, changed, sse);
-        }
-    }
+    if (blockIdx.x == 0)
+        head_tail<STATS>(e.a, h, nvb, changed, sse);
+    if (STATS)
+        block_stats(changed, sse, e.res, e.slot);
+}
+
+// Cover and stego at different addresses mod 16, out of place: aligned
+// stego vectors after h head bytes, each from two aligned cover vectors
+// (cover + h is 4Q + b bytes past a 16-byte boundary); block 0 does the head
+// and the tail (fewer than 32 bytes).  Requires n_bytes >= h.
+template <int Q, bool STATS>
+__global__ void __launch_bounds__(512) embed_funnel(EmbedArgs e, uint32_t h, uint32_t sel)
+{
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
+    unsigned long long changed = 0, sse = 0;
+    write_res(e, STATS);
+    const uint64_t nvb = (e.a.n_bytes - h) >> 4;
+    s1::embed_funnel_range<Q, STATS>(e.a, h, sel, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                     nvb, (uint64_t)gridDim.x * blockDim.x, changed, sse);
+    if (blockIdx.x == 0)
+        head_tail<STATS>(e.a, h, nvb, changed, sse);
     if (STATS)
         block_stats(changed, sse, e.res, e.slot);
 }
@@ -231,6 +259,22 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
         const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvb, (uint64_t)T * kShiftV);
         void *sargs[] = {&e, (void *)&h};
         return launch_dependent(k, dim3(grid), dim3(T), sargs, 0, s);
+    }
+    const uint32_t hs = (uint32_t)((16u - ((uintptr_t)stego & 15u)) & 15u);
+    if (cover != stego && n_bytes >= (uint64_t)hs + 16u) {
+        const uint32_t d = (uint32_t)(((uintptr_t)cover + hs) & 15u), b = d & 3u;
+        const uint32_t sel = b | ((b + 1) << 4) | ((b + 2) << 8) | ((b + 3) << 12);
+        const void *k;
+        switch (d >> 2) {
+        case 0: k = stats ? (const void *)embed_funnel<0, true> : (const void *)embed_funnel<0, false>; break;
+        case 1: k = stats ? (const void *)embed_funnel<1, true> : (const void *)embed_funnel<1, false>; break;
+        case 2: k = stats ? (const void *)embed_funnel<2, true> : (const void *)embed_funnel<2, false>; break;
+        default: k = stats ? (const void *)embed_funnel<3, true> : (const void *)embed_funnel<3, false>; break;
+        }
+        const uint64_t nvb = (n_bytes - hs) >> 4;
+        const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvb, (uint64_t)T);
+        void *fargs[] = {&e, (void *)&hs, (void *)&sel};
+        return launch_dependent(k, dim3(grid), dim3(T), fargs, 0, s);
     }
     const void *k = stats ? (const void *)embed_bytes<true> : (const void *)embed_bytes<false>;
     const uint64_t units = (n_bytes + 7) >> 3;

@@ -302,6 +302,44 @@ def test_same_misalignment_full_size(S, O):
     assert S.read_result(res2)["msg_bytes"] == m and torch.equal(out, msg)
 
 
+@pytest.mark.parametrize("d", range(1, 16))
+def test_different_misalignment_vector_path(S, O, d):
+    """Cover and stego at different addresses mod 16, out of place (each
+    aligned stego vector from two aligned cover vectors joined at byte d):
+    every relative offset d, stego offsets 0 and 9, header and raw, every
+    stream bit offset of the first vector."""
+    rng = np.random.default_rng(900 + d)
+    C = 3 * 4096 + 61
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    for so in (0, 9):
+        co = (so + d) % 16
+        for header in (True, False):
+            cap = S.stego_capacity(C, S.HEADER_BE32 if header else 0)
+            for m in sorted({0, 1, 3, 37, cap // 2 + 1, cap}):
+                msg = rng.integers(0, 256, m, dtype=np.uint8)
+                _embed_check(S, O, cover, msg, header, offs=(co, so, (co + so) % 4))
+
+
+def test_different_misalignment_full_size(S, O):
+    """The 8192x8192x3 cover at full capacity, the cover 3 and the stego 7
+    bytes past a 16-byte boundary, with statistics, against the oracle."""
+    w = synth.single_8192()
+    C = w.cover_bytes
+    cbuf = torch.empty(C + 16, dtype=torch.uint8, device="cuda")
+    sbuf = torch.empty(C + 16, dtype=torch.uint8, device="cuda")
+    cover = cbuf[3:3 + C]
+    cover.copy_(w.cover("cuda"))
+    stego = sbuf[7:7 + C]
+    msg = w.message("cuda")
+    res = S.new_result()
+    S.stego_embed(cover, stego, msg, S.HEADER_BE32 | S.FUSE_STATS, res)
+    c_h, m_h = cover.cpu().numpy(), msg.cpu().numpy()
+    st, want = O.stream1_embed(c_h, m_h, header=True)
+    assert st == 0 and np.array_equal(stego.cpu().numpy(), want)
+    r = S.read_result(res)
+    assert r["status"] == 0 and (r["changed"], r["sse"]) == O.changed_bytes(c_h, want)
+
+
 def test_single_8192_autotuned_shapes(S, O):
     """The full-size cover in the launch shapes the autotuner installs for
     the benchmark (register or staged kernels), every byte against the
