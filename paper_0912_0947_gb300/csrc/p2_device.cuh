@@ -497,6 +497,182 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
     }
 }
 
+// 16 bytes from global to shared memory without passing through registers
+// (completion per thread through commit and wait groups).
+__device__ __forceinline__ void cp_async16(uint4 *smem, const uint4 *gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Waits until at most N of the calling thread's committed groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// What one unit needs besides its cover vectors: how it is embedded (mode
+// 0 copy only, 1 one quarter, 2 per pixel), its column, row length,
+// quarter, message row and, in mode 1, its 16 message bytes.
+struct UnitJob {
+    uint32_t mode, colf, L, i0;
+    const uint8_t *mrow;
+    uint32_t m[4];
+};
+
+__device__ __forceinline__ void plan_unit(const View &a, uint32_t k, uint32_t k_end,
+                                          uint32_t carry, uint32_t r, uint32_t uc, UnitJob &J)
+{
+    J.mode = 0;
+    if (k < k_end && k < carry) {
+        J.colf = 16u * uc;
+        J.L = row_len(a, r);
+        J.mrow = a.msg_in + (uint64_t)r * a.Q;
+        J.i0 = quarter(J.colf, J.L);
+        if (J.colf + 15 < 4 * J.L && quarter(J.colf + 15, J.L) == J.i0) {
+            J.mode = 1;
+            load16(J.mrow + (J.colf - J.i0 * J.L), J.m);
+        } else {
+            J.mode = 2;
+        }
+    }
+}
+
+// units_embed for CH > 1 with a two-stage copy pipeline per warp: while the
+// warp embeds the units of one iteration from shared memory, the cover
+// vectors of its next iteration are already on their way there
+// (cp.async, memory order, coalesced) and the next units' message bytes on
+// their way to registers.  Same arguments and results as units_embed; CTAs
+// of at most 256 threads.
+template <int CH, int PLANE, bool STATS, int UT, bool INPLACE = false>
+__device__ __forceinline__ void units_embed_async(const View &a, uint32_t k_first,
+                                                  uint32_t k_end, uint32_t step,
+                                                  unsigned long long &changed,
+                                                  unsigned long long &sse)
+{
+    static_assert(CH > 1, "one-channel units are single vectors, loaded coalesced as they are");
+    const uint32_t upr = a.W / 16;
+    if (upr == 0)
+        return;
+    const uint32_t carry = carrying_units(a, upr);
+    if (INPLACE && k_end > carry)
+        k_end = carry;
+    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.src);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.dst);
+    const uint32_t lane = threadIdx.x & 31u;
+    constexpr uint32_t SV = unit_stage_slots<CH>();
+    constexpr uint32_t WS = 2 * UT * SV; // two stages per warp
+    __shared__ uint4 stage[kStageWarps * WS];
+    uint4 *const sw = stage + (threadIdx.x >> 5) * WS;
+    const uint64_t vend = (uint64_t)k_end * CH;
+    const uint32_t tr = blockDim.x / upr, tc = blockDim.x - tr * upr;
+    const uint32_t sr = step / upr, sc = step - sr * upr;
+    uint32_t r0 = k_first / upr, u0 = k_first - r0 * upr;
+
+    // the warp's vectors of the iteration at lane 0's unit kb -> stage s
+    auto issue = [&](uint32_t kb, uint32_t s) {
+#pragma unroll
+        for (int u = 0; u < UT; ++u) {
+            const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (v0 + 32u * j + lane < vend)
+                    cp_async16(sw + s * UT * SV + u * SV + unit_stage_slot<CH>(32u * j + lane),
+                               src + v0 + 32u * j + lane);
+        }
+        cp_async_commit();
+    };
+    auto plan = [&](uint32_t k0, uint32_t r, uint32_t uc, UnitJob (&J)[UT]) {
+#pragma unroll
+        for (int u = 0; u < UT; ++u) {
+            if (u > 0)
+                rc_add(r, uc, tr, tc, upr);
+            plan_unit(a, k0 + u * blockDim.x, k_end, carry, r, uc, J[u]);
+        }
+    };
+
+    uint32_t k0 = k_first; // the lane's first unit; k0 - lane is the same for the warp
+    if (k0 - lane >= k_end)
+        return;
+    UnitJob J[UT];
+    issue(k0 - lane, 0);
+    plan(k0, r0, u0, J);
+    uint32_t s = 0;
+    for (;;) {
+        const uint32_t kn = k0 + step;
+        const bool next = kn - lane < k_end; // kn < 2^32: units and steps stay below 2^31
+        UnitJob Jn[UT];
+        rc_add(r0, u0, sr, sc, upr);
+        if (next) {
+            issue(kn - lane, s ^ 1u);
+            plan(kn, r0, u0, Jn);
+            cp_async_wait<1>(); // this iteration's copies landed (the next may be pending)
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp(); // every lane's copies visible to the warp
+        uint4 *const st = sw + s * UT * SV;
+#pragma unroll
+        for (int u = 0; u < UT; ++u) {
+            const uint32_t k = k0 + u * blockDim.x;
+            if (k >= k_end)
+                continue;
+            uint4 o[CH];
+#pragma unroll
+            for (int q = 0; q < CH; ++q)
+                o[q] = st[u * SV + unit_stage_slot<CH>(CH * lane + q)];
+            uint32_t Gn[4], Go[4];
+            if (STATS && J[u].mode)
+                get_unit<CH, PLANE>(o, Go);
+            if (J[u].mode == 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    Gn[q] = J[u].m[q] >> (2 * J[u].i0);
+                put_unit<CH, PLANE>(o, Gn);
+            } else if (J[u].mode == 2) {
+                slow_unit<CH, PLANE, 0>(o, J[u].colf, J[u].L, J[u].mrow);
+                if (STATS)
+                    get_unit<CH, PLANE>(o, Gn);
+            }
+            if (STATS && J[u].mode) {
+                uint32_t n = 0, sq = 0;
+                plane_stats(Gn, Go, n, sq);
+                changed += n;
+                sse += sq;
+            }
+            if (J[u].mode) {
+#pragma unroll
+                for (int q = 0; q < CH; ++q)
+                    st[u * SV + unit_stage_slot<CH>(CH * lane + q)] = o[q];
+            }
+        }
+        __syncwarp(); // the rewritten units visible to the storing lanes
+#pragma unroll
+        for (int u = 0; u < UT; ++u) {
+            const uint64_t v0 = (uint64_t)(k0 - lane + u * blockDim.x) * CH;
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (v0 + 32u * j + lane < vend)
+                    __stcs(dst + v0 + 32u * j + lane, st[u * SV + unit_stage_slot<CH>(32u * j + lane)]);
+        }
+        if (!next)
+            break;
+        // stage s is refilled two iterations on, after this lane's reads of
+        // its own memory-order slots above
+#pragma unroll
+        for (int u = 0; u < UT; ++u)
+            J[u] = Jn[u];
+        k0 = kn;
+        s ^= 1u;
+    }
+}
+
 // Scatter of carrying rows r = r_first + i*r_step < min(r_end, R): the
 // calling CTA's threads split each row's L message bytes, four per thread in
 // flight; each reads B[r*Q + j] once and rewrites its four plane bytes (from

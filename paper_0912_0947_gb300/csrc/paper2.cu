@@ -4,8 +4,8 @@
 // per-row routines live in p2_device.cuh and are shared with the batched
 // kernels.
 //   p2_embed_units<CH,PLANE,STATS,INPLACE>  persistent grid over 16-pixel
-//       units; 256-thread CTAs, 2 per SM, each warp's units staged through
-//       shared memory.  Out of place one pass (2C + N bytes); in place the
+//       units; 256-thread CTAs, each warp's units copied to shared memory
+//       one iteration ahead (cp.async).  Out of place one pass (2C + N bytes); in place the
 //       units with carrying pixels, read and written back whole.
 //   p2_embed_rows  the scatter after a copy (and in place) for layouts the
 //       unit kernel does not take; CTAs stride over carrying rows.
@@ -44,11 +44,20 @@ __device__ __forceinline__ void write_res(const P2Args &a, bool stats)
 
 constexpr int kUnitThreads = 256; // at most 256: the staging area holds 8 warps
 constexpr int kUnitsPerThread = 2;
+constexpr int kAsyncUnits = 1; // units per thread and iteration of the copy pipeline (0: off)
+
+// Units one thread takes per iteration of p2_embed_units.
+int units_per_thread(uint32_t channels)
+{
+    return channels > 1 && kAsyncUnits > 0 ? kAsyncUnits : kUnitsPerThread;
+}
 
 // Out of place every unit of the image; in place the units with carrying
-// pixels.  Two CTAs per SM: the staged units take 107-112 registers, and
-// capped at 80 for three CTAs they spilled and ran slower (8192x8192x3,
-// plane 0: 70-72 against 67.6 us).
+// pixels.  Three or four channels run the two-stage copy pipeline
+// (units_embed_async: 79 registers, three CTAs per SM; 8192x8192x3, plane 0:
+// 63.7-65.5 us against 67.6 us with the register-staged units_embed, which
+// needed 107-112 registers and two CTAs per SM); one channel loads its
+// single-vector units directly.
 template <int CH, int PLANE, bool STATS, bool INPLACE>
 __global__ void __launch_bounds__(kUnitThreads, 2) p2_embed_units(P2Args a)
 {
@@ -57,9 +66,14 @@ __global__ void __launch_bounds__(kUnitThreads, 2) p2_embed_units(P2Args a)
     unsigned long long changed = 0, sse = 0;
     write_res(a, STATS);
     const uint32_t nunits = a.v.W / 16 * (INPLACE ? a.v.R : a.v.H);
-    p2::units_embed<CH, PLANE, STATS, kUnitsPerThread, INPLACE>(
-        a.v, blockIdx.x * blockDim.x * kUnitsPerThread + threadIdx.x, nunits,
-        gridDim.x * blockDim.x * kUnitsPerThread, changed, sse);
+    if constexpr (CH > 1 && kAsyncUnits > 0)
+        p2::units_embed_async<CH, PLANE, STATS, kAsyncUnits, INPLACE>(
+            a.v, blockIdx.x * blockDim.x * kAsyncUnits + threadIdx.x, nunits,
+            gridDim.x * blockDim.x * kAsyncUnits, changed, sse);
+    else
+        p2::units_embed<CH, PLANE, STATS, kUnitsPerThread, INPLACE>(
+            a.v, blockIdx.x * blockDim.x * kUnitsPerThread + threadIdx.x, nunits,
+            gridDim.x * blockDim.x * kUnitsPerThread, changed, sse);
     if (STATS)
         block_stats(changed, sse, a.res, a.slot);
 }
@@ -186,7 +200,7 @@ cudaError_t p2_embed_fused(const uint8_t *cover, uint8_t *stego, const stego_geo
                           : units_kernel<false, false>(g.channels, g.plane);
     const uint64_t nunits = (uint64_t)(g.width / 16u) * g.height;
     const int grid = persistent_grid(k, kUnitThreads, 0, kAnyCtas, nunits ? nunits : 1,
-                                     (uint64_t)kUnitThreads * kUnitsPerThread);
+                                     (uint64_t)kUnitThreads * units_per_thread(g.channels));
     void *args[] = {&a};
     return launch_dependent(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
 }
@@ -205,7 +219,7 @@ cudaError_t p2_embed(const uint8_t *cover, uint8_t *stego, const stego_geom &g,
         const uint64_t nunits = (uint64_t)(g.width / 16u) * a.v.R;
         const int grid = persistent_grid(k, kUnitThreads, 0, kAnyCtas,
                                          nunits ? nunits : 1,
-                                         (uint64_t)kUnitThreads * kUnitsPerThread);
+                                         (uint64_t)kUnitThreads * units_per_thread(g.channels));
         void *args[] = {&a};
         return launch_dependent(k, dim3(grid), dim3(kUnitThreads), args, 0, s);
     }
