@@ -5,8 +5,9 @@
 // kernels.
 //   p2_embed_units<CH,PLANE,STATS,INPLACE>  persistent grid over 16-pixel
 //       units; 256-thread CTAs, each warp's units copied to shared memory
-//       one iteration ahead (cp.async).  Out of place one pass (2C + N bytes); in place the
-//       units with carrying pixels, read and written back whole.
+//       one iteration ahead (cp.async).  Out of place one pass (2C + N
+//       bytes); in place the units with carrying pixels, read and written
+//       back whole.
 //   p2_embed_rows  the scatter after a copy (and in place) for layouts the
 //       unit kernel does not take; CTAs stride over carrying rows.
 //   p2_extract_units<CH,PLANE>  runs of 16 message bytes (CH in {1,3,4}).
