@@ -20,6 +20,7 @@
 //         channel count; in place; after a copy out of place).
 #pragma once
 
+#include "async_copy.cuh"
 #include "internal.cuh"
 
 namespace stego {
@@ -495,26 +496,6 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
         if constexpr (TRACK)
             rc_add(r0, u0, sr, sc, upr);
     }
-}
-
-// 16 bytes from global to shared memory without passing through registers
-// (completion per thread through commit and wait groups).
-__device__ __forceinline__ void cp_async16(uint4 *smem, const uint4 *gmem)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// Waits until at most N of the calling thread's committed groups are pending.
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // What one unit needs besides its cover vectors: how it is embedded (mode

@@ -26,6 +26,7 @@
 // bit l from its carrying byte and one ballot gathers them.
 #include <cstring>
 
+#include "async_copy.cuh"
 #include "s1_device.cuh"
 
 namespace stego {
@@ -436,6 +437,135 @@ __global__ void __launch_bounds__(512) embedk_units(KView a)
         block_stats(changed, sse, a.res, a.slot);
 }
 
+// Plane units (CH = 3 or 4) with a two-stage copy pipeline per warp: while
+// the warp embeds the units of one iteration from shared memory, the cover
+// vectors of its next iteration are on their way there (cp.async, memory
+// order, coalesced: a lane's own unit is 16*CH bytes from its neighbour's)
+// and the next units' stream windows on their way to registers.  Each lane
+// then takes its unit from shared memory, embeds it as embedk_units does and
+// writes it back; the warp stores its vectors in memory order.  CTAs of at
+// most kAsyncThreads threads (the staging area holds that many warps).
+constexpr int kAsyncThreads = 256;
+template <int K, int CH, int PLANE, bool STATS>
+__global__ void __launch_bounds__(kAsyncThreads) embedk_units_async(KView a)
+{
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
+    static_assert(CH > 1, "plane units only");
+    constexpr uint32_t MASK = (1u << K) - 1u;
+    constexpr uint32_t BYTEMASK = MASK * 0x01010101u;
+    constexpr uint32_t SV = unit_stage_slots<CH>();
+    __shared__ uint4 stage[(kAsyncThreads / 32) * 2 * SV];
+    uint4 *const sw = stage + (threadIdx.x >> 5) * 2 * SV;
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned long long changed = 0, sse = 0;
+    embed_res(a, STATS);
+    const uint64_t nunits = a.n_carry >> 4;
+    const uint64_t vend = nunits * CH;
+    const uint4 *__restrict__ cv = reinterpret_cast<const uint4 *>(a.cover);
+    uint4 *const ov = reinterpret_cast<uint4 *>(a.stego);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    auto issue = [&](uint64_t ub, uint32_t s) { // the warp's vectors from unit ub -> stage s
+        const uint64_t v0 = ub * CH;
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            if (v0 + 32u * j + lane < vend)
+                cp_async16(sw + s * SV + unit_stage_slot<CH>(32u * j + lane), cv + v0 + 32u * j + lane);
+        cp_async_commit();
+    };
+    auto window = [&](uint64_t u) {
+        return (u < nunits && u < a.full_units) ? stream_window<K>(a, u) : 0ull;
+    };
+    uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; // u - lane: the same for the warp
+    if (u - lane < nunits) {
+        issue(u - lane, 0);
+        uint64_t X = window(u);
+        uint32_t s = 0;
+        for (;;) {
+            const uint64_t un = u + step;
+            const bool next = un - lane < nunits;
+            uint64_t Xn = 0;
+            if (next) {
+                issue(un - lane, s ^ 1u);
+                Xn = window(un);
+                cp_async_wait<1>(); // this iteration's copies landed (the next may be pending)
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp(); // every lane's copies visible to the warp
+            uint4 *const st = sw + s * SV;
+            if (u < nunits && u < a.part_units) {
+                uint32_t w[4 * CH];
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const uint4 t = st[unit_stage_slot<CH>(CH * lane + q)];
+                    w[4 * q] = t.x;
+                    w[4 * q + 1] = t.y;
+                    w[4 * q + 2] = t.z;
+                    w[4 * q + 3] = t.w;
+                }
+                uint32_t c[4], o[4];
+                gather_unit<CH, PLANE>(w, c);
+                if (u < a.full_units) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        o[i] = (c[i] & ~BYTEMASK) | unit_fields<K>(X, i);
+                } else {
+                    const uint4 e = stream_end_vector(a, u, make_uint4(c[0], c[1], c[2], c[3]));
+                    o[0] = e.x;
+                    o[1] = e.y;
+                    o[2] = e.z;
+                    o[3] = e.w;
+                }
+                uint32_t d[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    d[i] = o[i] ^ c[i];
+                if (STATS)
+                    unit_stats<K>(o, c, d, changed, sse);
+                scatter_xor<CH, PLANE>(w, d);
+#pragma unroll
+                for (int q = 0; q < CH; ++q)
+                    st[unit_stage_slot<CH>(CH * lane + q)] =
+                        make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            }
+            __syncwarp(); // the rewritten units visible to the storing lanes
+            const uint64_t v0 = (u - lane) * CH;
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (v0 + 32u * j + lane < vend)
+                    __stcs(ov + v0 + 32u * j + lane, st[unit_stage_slot<CH>(32u * j + lane)]);
+            if (!next)
+                break;
+            // stage s is refilled two iterations on, after this lane's reads
+            // of its own memory-order slots above
+            X = Xn;
+            u = un;
+            s ^= 1u;
+        }
+    }
+    // cover bytes of the carrying bytes after the last whole unit: plane
+    // bytes take their field, the other bytes of those pixels are copied
+    if (blockIdx.x == 0 && threadIdx.x < (uint32_t)(a.n_carry & 15u) * CH) {
+        const uint64_t pbyte = ((a.n_carry >> 4) << 4) * CH + threadIdx.x;
+        const uint32_t cb = a.cover[pbyte];
+        uint32_t ob = cb;
+        if (threadIdx.x % CH == PLANE) {
+            uint32_t fv, fm;
+            field_of(a, pbyte / CH, fv, fm);
+            ob = (cb & ~fm) | (fv & fm);
+        }
+        a.stego[pbyte] = (uint8_t)ob;
+        if (STATS) {
+            const uint32_t dd = ob > cb ? ob - cb : cb - ob;
+            changed += dd != 0;
+            sse += dd * dd;
+        }
+    }
+    if (STATS)
+        block_stats(changed, sse, a.res, a.slot);
+}
+
 // One thread per carrying byte x < n_carry (all bytes: the bytes past the
 // stream are copied; one plane: only plane bytes are written).
 template <bool STATS>
@@ -626,16 +756,16 @@ const void *embed_units_for(uint32_t ch, uint32_t plane)
         return (const void *)embedk_units<K, 1, 0, STATS>;
     if (ch == 3) {
         switch (plane) {
-        case 0: return (const void *)embedk_units<K, 3, 0, STATS>;
-        case 1: return (const void *)embedk_units<K, 3, 1, STATS>;
-        default: return (const void *)embedk_units<K, 3, 2, STATS>;
+        case 0: return (const void *)embedk_units_async<K, 3, 0, STATS>;
+        case 1: return (const void *)embedk_units_async<K, 3, 1, STATS>;
+        default: return (const void *)embedk_units_async<K, 3, 2, STATS>;
         }
     }
     switch (plane) {
-    case 0: return (const void *)embedk_units<K, 4, 0, STATS>;
-    case 1: return (const void *)embedk_units<K, 4, 1, STATS>;
-    case 2: return (const void *)embedk_units<K, 4, 2, STATS>;
-    default: return (const void *)embedk_units<K, 4, 3, STATS>;
+    case 0: return (const void *)embedk_units_async<K, 4, 0, STATS>;
+    case 1: return (const void *)embedk_units_async<K, 4, 1, STATS>;
+    case 2: return (const void *)embedk_units_async<K, 4, 2, STATS>;
+    default: return (const void *)embedk_units_async<K, 4, 3, STATS>;
     }
 }
 
@@ -720,9 +850,10 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
                                  : embed_units_kernel<false>(k, a.channels, a.plane);
         const uint64_t nunits = a.n_carry >> 4;
         const int per_thread = a.channels == 1 ? kEmbedAllBytesUnits : 1;
-        const int grid = persistent_grid(kern, T, 0, kAnyCtas, nunits ? nunits : 1,
-                                         (uint64_t)T * per_thread);
-        return launch_dependent(kern, dim3(grid), dim3(T), args, 0, s);
+        const int TU = a.channels == 1 ? T : kAsyncThreads; // plane units: the pipeline's CTAs
+        const int grid = persistent_grid(kern, TU, 0, kAnyCtas, nunits ? nunits : 1,
+                                         (uint64_t)TU * per_thread);
+        return launch_dependent(kern, dim3(grid), dim3(TU), args, 0, s);
     }
     if (plane_only && !inplace) {
         // the non-carrying bytes come from a copy of the cover (a stream
