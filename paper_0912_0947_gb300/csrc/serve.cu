@@ -270,9 +270,11 @@ struct stego_server {
                 break;
             if (!a && !b) {
                 if (busy) {
-                    // batches in flight: poll their events again shortly
+                    // batches in flight: poll their events again at once
+                    // (a sleep, however short, lasts the timer slack: some
+                    // 50 us on Linux)
                     lk.unlock();
-                    std::this_thread::sleep_for(std::chrono::microseconds(5));
+                    std::this_thread::yield();
                 } else {
                     cv_work.wait_for(lk, std::chrono::milliseconds(2));
                 }
