@@ -40,16 +40,20 @@ def test_stego_of_stego_chain(S, O):
     d_msgs = [torch.from_numpy(m).cuda() for m in msgs]
     outs = [torch.full((cap,), 0xEE, dtype=torch.uint8, device="cuda") for _ in msgs]
     res = [S.new_result() for _ in msgs]
+    eres = [S.new_result() for _ in msgs]
     torch.cuda.synchronize()
     for i, m in enumerate(d_msgs):
         src, dst = bufs[i % 2], bufs[(i + 1) % 2]
-        S.stego_embed(src, dst, m, S.HEADER_BE32 | S.FUSE_STATS)
+        S.stego_embed(src, dst, m, S.HEADER_BE32 | S.FUSE_STATS, eres[i])
         S.stego_extract(dst, outs[i], 0, S.HEADER_BE32, res[i])
     torch.cuda.synchronize()
     want = cover
-    for m in msgs:
-        st, want = O.stream1_embed(want, m, header=True)
+    for i, m in enumerate(msgs):
+        st, nxt = O.stream1_embed(want, m, header=True)
         assert st == oracle.OK
+        r = S.read_result(eres[i])
+        assert r["status"] == 0 and (r["changed"], r["sse"]) == O.changed_bytes(want, nxt), i
+        want = nxt
     assert np.array_equal(bufs[len(msgs) % 2].cpu().numpy(), want)
     for i, m in enumerate(msgs):
         r = S.read_result(res[i])
@@ -83,14 +87,15 @@ def test_in_place_mixed_chain(S, O):
     torch.cuda.synchronize()
     for kind, m in ops:
         dm = torch.from_numpy(m).cuda()
-        keep.append(dm)
+        r = S.new_result()
+        keep += [dm, r]
         if kind == "s1":
-            S.stego_embed(buf, buf, dm, S.HEADER_BE32 | S.FUSE_STATS)
+            S.stego_embed(buf, buf, dm, S.HEADER_BE32 | S.FUSE_STATS, r)
         elif kind == "k2plane":
             S.stego_embed(buf, buf, dm, S.BITS(2) | S.HEADER_BE32 | S.PLANE_ONLY | S.FUSE_STATS,
-                          geom=geom)
+                          r, geom=geom)
         elif kind == "paper":
-            S.stego_embed(buf, buf, dm, S.LAYOUT_PAPER2 | S.FUSE_STATS, geom=geom)
+            S.stego_embed(buf, buf, dm, S.LAYOUT_PAPER2 | S.FUSE_STATS, r, geom=geom)
         else:
             d = S.descs_to_device(S.pack_descs([dict(cover=buf, stego=buf, msg=dm,
                                                      cover_bytes=C, msg_bytes=m.size,
