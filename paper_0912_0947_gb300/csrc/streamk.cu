@@ -56,6 +56,8 @@ struct KView {
     uint32_t msg_w4;      // embed: msg - (header bytes) is 4-byte aligned
     uint32_t msg_w2;      // embed: msg - (header bytes) is 2-byte aligned
     StatSlot *slot;       // embed: per-stream statistics slot or nullptr
+    uint32_t kmul;        // embed: 1 << k (a multiplier the compiler cannot see)
+    uint32_t pad;
 };
 
 __device__ __forceinline__ uint64_t carry_pos(const KView &a, uint64_t x)
@@ -114,25 +116,45 @@ __device__ __forceinline__ void embed_res(const KView &a, bool stats)
 // equals the count.
 template <int K>
 __device__ __forceinline__ void unit_stats(const uint32_t (&o)[4], const uint32_t (&c)[4],
-                                           const uint32_t (&d)[4], unsigned long long &changed,
+                                           const uint32_t (&d)[4], uint32_t kmul,
+                                           unsigned long long &changed,
                                            unsigned long long &sse)
 {
     constexpr uint32_t BM = ((1u << K) - 1u) * 0x01010101u;
-    uint32_t flags = 0, s = 0;
+    uint32_t n, s = 0;
+    if constexpr (K <= 2) {
+        // the four words' K-bit changes in disjoint bit ranges of each byte
+        // (word i at bits K*i), joined by multiply-adds, then one fold
+        // Horner in kmul = 1 << K: multiply-adds (FMA pipe), not shifts on
+        // the busy ALU pipe; kmul comes from the launch arguments so the
+        // compiler keeps the multiplies
+        const uint32_t acc0 = ((d[3] * kmul + d[2]) * kmul + d[1]) * kmul + d[0];
+        uint32_t acc = acc0;
+        if (K == 2)
+            acc = (acc | (acc >> 1)) & 0x55555555u;
+        n = __popc(acc);
+    } else {
+        uint32_t flags = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        uint32_t f = d[i];
-        if (K > 1)
+        for (int i = 0; i < 4; ++i) {
+            uint32_t f = d[i];
             f |= f >> 1;
-        if (K > 2)
-            f |= f >> 2; // bits 0..3 of each byte folded for K = 3, 4
-        flags |= (f & 0x01010101u) << i;
-        if (K > 1) {
-            const uint32_t ad = __vabsdiffu4(o[i] & BM, c[i] & BM);
-            s = __dp4a(ad, ad, s);
+            f |= f >> 2; // bits 0..3 of each byte folded
+            flags |= (f & 0x01010101u) << i;
         }
+        n = __popc(flags);
     }
-    const uint32_t n = __popc(flags);
+    if (K > 1) {
+        uint32_t ab = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { // sum of (a - b)^2 = a.a + b.b - 2 a.b over the fields
+            const uint32_t fa = o[i] & BM, fb = c[i] & BM;
+            s = __dp4a(fa, fa, s);
+            s = __dp4a(fb, fb, s);
+            ab = __dp4a(fa, fb, ab);
+        }
+        s -= 2u * ab;
+    }
     changed += n;
     sse += K > 1 ? s : n;
 }
@@ -270,7 +292,7 @@ __device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
         // stream byte i; lane l takes its bits 7-2l and 6-2l: the products
         // b << 10l occupy disjoint bit ranges, and bits 8l+6, 8l+7 of their
         // sum hold pair l (b's bits 7-2l, 6-2l)
-        const uint32_t b = (hi >> (24 - 8 * i)) & 0xFFu;
+        const uint32_t b = __byte_perm(hi, 0u, 0x4440u | (3 - i)); // (hi >> (24 - 8i)) & 0xFF
         return ((b * 0x40100401u) >> 6) & 0x03030303u;
     } else if constexpr (K == 4) {
         // stream bytes 2i, 2i+1; lanes take high nibble, low nibble, high, low
@@ -409,7 +431,7 @@ __global__ void __launch_bounds__(512) embedk_units(KView a)
                 for (int i = 0; i < 4; ++i)
                     d[i] = o[i] ^ c[i];
                 if (STATS)
-                    unit_stats<K>(o, c, d, changed, sse);
+                    unit_stats<K>(o, c, d, a.kmul, changed, sse);
                 scatter_xor<CH, PLANE>(w[r], d);
             }
             store_unit<CH>(a.stego, u, w[r]);
@@ -522,7 +544,7 @@ __global__ void __launch_bounds__(kAsyncThreads) embedk_units_async(KView a)
                 for (int i = 0; i < 4; ++i)
                     d[i] = o[i] ^ c[i];
                 if (STATS)
-                    unit_stats<K>(o, c, d, changed, sse);
+                    unit_stats<K>(o, c, d, a.kmul, changed, sse);
                 scatter_xor<CH, PLANE>(w, d);
 #pragma unroll
                 for (int q = 0; q < CH; ++q)
@@ -838,6 +860,7 @@ cudaError_t sk_embed(const uint8_t *cover, uint8_t *stego, uint64_t C, uint32_t 
     a.part_units = (a.t_bits + 16u * k - 1) / (16u * k);
     a.msg_w4 = (((uintptr_t)msg - (header ? 4u : 0u)) & 3u) == 0;
     a.msg_w2 = (((uintptr_t)msg - (header ? 4u : 0u)) & 1u) == 0;
+    a.kmul = 1u << k;
     const bool inplace = cover == stego;
     const uint64_t t_carry = (a.t_bits + k - 1) / k; // carrying bytes the stream uses
     const int T = sh.threads;
