@@ -122,6 +122,7 @@ __device__ __forceinline__ void unit_stats(const uint32_t (&o)[4], const uint32_
 {
     constexpr uint32_t BM = ((1u << K) - 1u) * 0x01010101u;
     uint32_t n, s = 0;
+    static_assert(K >= 1 && K <= 4, "one to four bits per byte");
     if constexpr (K <= 2) {
         // the four words' K-bit changes in disjoint bit ranges of each byte
         // (word i at bits K*i), joined by multiply-adds, then one fold
@@ -134,15 +135,13 @@ __device__ __forceinline__ void unit_stats(const uint32_t (&o)[4], const uint32_
             acc = (acc | (acc >> 1)) & 0x55555555u;
         n = __popc(acc);
     } else {
-        uint32_t flags = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            uint32_t f = d[i];
-            f |= f >> 1;
-            f |= f >> 2; // bits 0..3 of each byte folded
-            flags |= (f & 0x01010101u) << i;
-        }
-        n = __popc(flags);
+        // k = 3, 4: two words per byte (word 2j+1 at bit K), then a field is
+        // nonzero when its top bit is set or its low K-1 bits plus all ones
+        // carry into the top bit (no carry leaves a field)
+        constexpr uint32_t LOW = K == 4 ? 0x77777777u : 0x1B1B1B1Bu;
+        constexpr uint32_t TOP = K == 4 ? 0x88888888u : 0x24242424u;
+        const uint32_t a01 = d[1] * kmul + d[0], a23 = d[3] * kmul + d[2];
+        n = __popc((a01 | ((a01 & LOW) + LOW)) & TOP) + __popc((a23 | ((a23 & LOW) + LOW)) & TOP);
     }
     if (K > 1) {
         uint32_t ab = 0;
