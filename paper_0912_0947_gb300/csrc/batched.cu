@@ -465,11 +465,12 @@ __device__ __forceinline__ void paper_embed_tile(const stego_desc &D, const Desc
         const uint64_t units = (uint64_t)(inf.W / 16u) * (ip ? v.R : inf.H);
         const uint32_t k0 = (uint32_t)b0 + threadIdx.x;
         const uint32_t k1 = (uint32_t)(b1 < units ? b1 : units);
-        // one unit per thread, not staged through shared memory: under the
-        // 80-register cap the staged form spilled more and ran slower (600
-        // video frames: 1.53 against 1.26 ms)
+        // one unit per thread, loaded by the thread itself: under the
+        // 80-register cap a form staged through shared memory spilled more
+        // and ran slower (600 video frames: 1.53 against 1.26 ms), and so did
+        // the cp.async pipeline of the single-cover kernel (1.34-1.83 ms)
         if (inf.channels == 3)
-            p2::units_embed<3, 0, STATS, 1, false, false>(v, k0, k1, blockDim.x, changed, sse);
+            p2::units_embed<3, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
         else
             p2::units_embed<1, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
         return;

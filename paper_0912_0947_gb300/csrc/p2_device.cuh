@@ -322,21 +322,19 @@ __device__ __forceinline__ uint32_t carrying_units(const View &a, uint32_t upr)
     return a.R ? (a.R - 1) * upr + (a.L_last + 3) / 4 : 0u;
 }
 
-constexpr int kStageWarps = 8; // units_embed runs in CTAs of at most 256 threads
+constexpr int kStageWarps = 8; // units_embed_async runs in CTAs of at most 256 threads
 
 // One pass over units k = k_first + i*step (+ u*blockDim.x, u < UT),
 // k < k_end, of an image whose rows are whole units and whose buffers are
-// 16-byte aligned; the lanes of a warp start at 32 consecutive units (k_first
-// = base + threadIdx.x).  STAGED with CH > 1 (CTAs of at most 256 threads),
-// the warp loads and stores its units' 32*CH vectors in memory order
-// (coalesced: a lane's own unit is 16*CH bytes apart from its neighbour's)
-// and exchanges them through shared memory, so each lane works on its own
-// unit in registers.  Every load of an iteration (cover, then
-// message) is issued before any arithmetic.  Out of place every unit is
-// written (units without carrying pixels are copied); in place (INPLACE)
-// k_end is cut to the carrying units, each vector read and written back by
-// the same lane.
-template <int CH, int PLANE, bool STATS, int UT, bool INPLACE = false, bool STAGED = true>
+// 16-byte aligned, each thread on its own units: every load of an iteration
+// (cover, then message) is issued before any arithmetic.  With one channel
+// the lanes' single-vector units are consecutive (coalesced); with three or
+// four a lane's unit lies 16*CH bytes from its neighbour's, which
+// units_embed_async avoids and the batched kernels accept for their register
+// budget.  Out of place every unit is written (units without carrying pixels
+// are copied); in place (INPLACE) k_end is cut to the carrying units, each
+// unit read and written back by the same thread.
+template <int CH, int PLANE, bool STATS, int UT, bool INPLACE = false>
 __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uint32_t k_end,
                                             uint32_t step, unsigned long long &changed,
                                             unsigned long long &sse)
@@ -349,13 +347,7 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
         k_end = carry;
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.src);
     uint4 *dst = reinterpret_cast<uint4 *>(a.dst);
-    const uint32_t lane = threadIdx.x & 31u;
-    constexpr bool STAGE = STAGED && CH > 1;
-    constexpr uint32_t SV = unit_stage_slots<CH>(); // slots per warp and unit group
-    __shared__ uint4 stage[STAGE ? kStageWarps * UT * SV : 1];
-    uint4 *const sw = stage + (threadIdx.x >> 5) * UT * SV;
-    const uint64_t vend = (uint64_t)k_end * CH;
-    // row and unit column of the lane's unit: with several units per thread
+    // row and unit column of the thread's unit: with several units per thread
     // kept by additions (the strides blockDim.x and step in whole rows and
     // remaining units), with one unit divided out (fewer live registers)
     constexpr bool TRACK = UT > 1;
@@ -368,26 +360,15 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
         sr = step / upr;
         sc = step - sr * upr;
     }
-    // staged, the loop runs on the warp's first unit kb (the same for every
-    // lane, so every lane runs every iteration); else on the lane's own
-    for (uint32_t k0 = k_first; (STAGE ? k0 - lane : k0) < k_end; k0 += step) {
-        const uint32_t kb = k0 - lane;
+    for (uint32_t k0 = k_first; k0 < k_end; k0 += step) {
         uint4 c[UT][CH];
 #pragma unroll
         for (int u = 0; u < UT; ++u) {
-            if constexpr (STAGE) { // the warp's vectors in memory order
-                const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
+            const uint32_t k = k0 + u * blockDim.x;
+            if (k < k_end) {
 #pragma unroll
-                for (int j = 0; j < CH; ++j)
-                    if (v0 + 32u * j + lane < vend)
-                        c[u][j] = __ldcs(src + v0 + 32u * j + lane);
-            } else { // the lane's own unit
-                const uint32_t k = k0 + u * blockDim.x;
-                if (k < k_end) {
-#pragma unroll
-                    for (int q = 0; q < CH; ++q)
-                        c[u][q] = __ldcs(src + (uint64_t)k * CH + q);
-                }
+                for (int q = 0; q < CH; ++q)
+                    c[u][q] = __ldcs(src + (uint64_t)k * CH + q);
             }
         }
         int mode[UT]; // 0: copy only, 1: one quarter (SWAR), 2: per pixel
@@ -415,26 +396,6 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
                     load16(mrow[u] + (colf[u] - i0[u] * L[u]), m[u]);
                 } else {
                     mode[u] = 2;
-                }
-            }
-        }
-        if constexpr (STAGE) {
-            __syncwarp(); // the previous iteration's stores have read their slots
-#pragma unroll
-            for (int u = 0; u < UT; ++u) {
-                const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
-#pragma unroll
-                for (int j = 0; j < CH; ++j)
-                    if (v0 + 32u * j + lane < vend)
-                        sw[u * SV + unit_stage_slot<CH>(32u * j + lane)] = c[u][j];
-            }
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < UT; ++u) {
-                if (k0 + u * blockDim.x < k_end) {
-#pragma unroll
-                    for (int q = 0; q < CH; ++q)
-                        c[u][q] = sw[u * SV + unit_stage_slot<CH>(CH * lane + q)];
                 }
             }
         }
@@ -471,27 +432,9 @@ __device__ __forceinline__ void units_embed(const View &a, uint32_t k_first, uin
                 changed += n;
                 sse += sq;
             }
-            if constexpr (STAGE) {
 #pragma unroll
-                for (int q = 0; q < CH; ++q)
-                    sw[u * SV + unit_stage_slot<CH>(CH * lane + q)] = o[q];
-            } else {
-#pragma unroll
-                for (int q = 0; q < CH; ++q)
-                    __stcs(dst + (uint64_t)k * CH + q, o[q]);
-            }
-        }
-        if constexpr (STAGE) {
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < UT; ++u) {
-                const uint64_t v0 = (uint64_t)(kb + u * blockDim.x) * CH;
-#pragma unroll
-                for (int j = 0; j < CH; ++j)
-                    if (v0 + 32u * j + lane < vend)
-                        __stcs(dst + v0 + 32u * j + lane,
-                               sw[u * SV + unit_stage_slot<CH>(32u * j + lane)]);
-            }
+            for (int q = 0; q < CH; ++q)
+                __stcs(dst + (uint64_t)k * CH + q, o[q]);
         }
         if constexpr (TRACK)
             rc_add(r0, u0, sr, sc, upr);
