@@ -19,6 +19,9 @@
 // holds every slot's descriptors, results and workspace; the server
 // allocates no device memory.  Per slot it keeps pinned host copies of the
 // descriptors and results (allocated once, at creation).
+#ifdef __linux__
+#include <sys/prctl.h>
+#endif
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -103,6 +106,7 @@ struct stego_server {
     uint64_t outstanding = 0;    // submitted, not yet completed
     uint64_t batches = 0;
     bool stop = false;
+    double t_last_launch = -1.0; // dispatcher thread only
     std::thread th;
 
     double now() const
@@ -247,6 +251,7 @@ struct stego_server {
             if (cudaEventRecord(s.done, s.stream) != cudaSuccess && s.launch_status == STEGO_OK)
                 s.launch_status = STEGO_E_CUDA;
             s.busy = true;
+            t_last_launch = now();
             {
                 std::lock_guard<std::mutex> lk(mu);
                 ++batches;
@@ -259,6 +264,11 @@ struct stego_server {
     void loop()
     {
         cudaSetDevice(device);
+#ifdef __linux__
+        // this thread's sleeps end within 1 us of their time instead of the
+        // default 50 us timer slack (a per-thread setting)
+        prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
         for (;;) {
             const bool a = reap();
             const bool b = dispatch();
@@ -270,11 +280,14 @@ struct stego_server {
                 break;
             if (!a && !b) {
                 if (busy) {
-                    // batches in flight: poll their events again at once
-                    // (a sleep, however short, lasts the timer slack: some
-                    // 50 us on Linux)
+                    // batches in flight: poll their events at once for the
+                    // first 50 us after a launch (where most batches end),
+                    // then every 2 us without holding a core
                     lk.unlock();
-                    std::this_thread::yield();
+                    if (now() - t_last_launch < 50e-6)
+                        std::this_thread::yield();
+                    else
+                        std::this_thread::sleep_for(std::chrono::microseconds(2));
                 } else {
                     cv_work.wait_for(lk, std::chrono::milliseconds(2));
                 }
