@@ -110,10 +110,9 @@ __device__ __forceinline__ void embed_res(const KView &a, bool stats)
 
 // Changed bytes and squared error of a unit's 16 carrying bytes (c before,
 // o after, d = o ^ c, differences in the low K bits only), summed in 32 bits
-// per unit.  A byte changed when any of its low K bits did: the K bits are
-// folded into bit 0 and the four words' flags packed into one word for one
-// population count.  With K = 1 every change is +-1, so the squared error
-// equals the count.
+// per unit.  A byte changed when any of its low K bits did (the packing and
+// the per-field test are below).  With K = 1 every change is +-1, so the
+// squared error equals the count.
 template <int K>
 __device__ __forceinline__ void unit_stats(const uint32_t (&o)[4], const uint32_t (&c)[4],
                                            const uint32_t (&d)[4], uint32_t kmul,
