@@ -127,3 +127,38 @@ def test_header_compiles_as_c():
                         "-I" + os.path.join(os.path.dirname(here), "include"),
                         "-I" + os.path.join(cuda, "include")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_capacity_is_the_oracles_boundary(built):
+    """stego_capacity (host code of the library) for every layout, header
+    choice, bits per byte and plane against the oracle: a message of the
+    reported capacity embeds, one byte more is refused."""
+    import numpy as np
+    import oracle
+    import paper_0912_0947_gb300 as S
+    O = oracle.load()
+    rng = np.random.default_rng(77)
+    geoms = [(7, 5, 3, 2), (16, 3, 1, 0), (33, 2, 4, 1), (5, 9, 3, 0), (64, 1, 3, 1)]
+    for W, H, ch, plane in geoms:
+        C = W * H * ch
+        cover = rng.integers(0, 256, C, dtype=np.uint8)
+        for k in (1, 2, 3, 4):
+            for header in (True, False):
+                for plane_only in (False, True):
+                    flags = S.BITS(k) | (S.HEADER_BE32 if header else 0) | \
+                        (S.PLANE_ONLY if plane_only else 0)
+                    g = (W, H, ch, plane) if plane_only else None
+                    cap = S.stego_capacity(C, flags, geom=g)
+                    ok = rng.integers(0, 256, cap, dtype=np.uint8)
+                    over = rng.integers(0, 256, cap + 1, dtype=np.uint8)
+                    st, _ = O.streamk_embed(cover, ok, k, header=header, geom=g)
+                    assert st == oracle.OK, (W, H, ch, plane, k, header, plane_only, cap)
+                    st, _ = O.streamk_embed(cover, over, k, header=header, geom=g)
+                    assert st != oracle.OK, (W, H, ch, plane, k, header, plane_only, cap)
+        cap = S.stego_capacity(C, S.LAYOUT_PAPER2, (W, H, ch, plane))
+        assert cap == O.paper2_capacity(W, H)
+        st, _ = O.paper2_embed(cover, W, H, ch, plane, rng.integers(0, 256, cap, dtype=np.uint8))
+        assert st == oracle.OK
+        st, _ = O.paper2_embed(cover, W, H, ch, plane,
+                               rng.integers(0, 256, cap + 1, dtype=np.uint8))
+        assert st != oracle.OK
