@@ -36,6 +36,13 @@
  *     the library allocates no device memory in any call.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous and stream-ordered; none synchronises the device.
+ *   - Kernels are launched as programmatic dependent launches: each waits
+ *     for the previous grid in the stream before touching memory, and lets
+ *     the next grid start launching early.  A caller's own kernel launched
+ *     after a call with the programmatic stream serialization attribute must
+ *     therefore wait (cudaGridDependencySynchronize / griddepcontrol.wait)
+ *     before reading the call's outputs, as any such launch must; ordinary
+ *     launches, copies and events see plain stream order.
  *   - Errors detectable from the arguments (null pointers, sizes, capacity,
  *     geometry, flags, overlapping buffers) are returned synchronously and
  *     nothing is launched or written.  Errors that depend on device data (a
