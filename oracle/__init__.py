@@ -170,6 +170,11 @@ class Oracle:
         return st, (msg[:N].copy() if st == OK else np.zeros(0, np.uint8))
 
     # -- statistics ------------------------------------------------------
+    def psnr(self, sse: int, n: int) -> float:
+        """The module-level ``psnr``; a method so that the pins can be run
+        against a handle whose PSNR formula has been replaced."""
+        return psnr(sse, n)
+
     def changed_bytes(self, a, b):
         a = np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
         b = np.ascontiguousarray(b, dtype=np.uint8).reshape(-1)
@@ -181,7 +186,9 @@ class Oracle:
 
 
 def psnr(sse: int, n: int) -> float:
-    """Section VIII quality measure: MSE over all n cover bytes, peak 255."""
+    """Section VIII quality measure: PSNR = 10 log10(peak^2 / MSE) with peak
+    255 (uint8) and MSE = sse / n, the squared error averaged over all n
+    cover bytes (every channel); infinite for an unchanged cover."""
     if sse == 0:
         return math.inf
     return 10.0 * math.log10(255.0 * 255.0 * n / sse)

@@ -16,7 +16,8 @@ What pins what:
   * invariants -- round trip, non-LSB bits unchanged, bytes past the message
     untouched, |stego - cover| <= 1 (<= 3 for two bits), sse == changed;
   * the Section VIII session shape (a 1024-byte row carrying a 7x8 secret
-    flattened column-major) and the Section VIII PSNR gap.
+    flattened column-major), the Section VIII PSNR gap, and the absolute
+    PSNR scale from its definition on hand-worked (sse, n) pairs.
 """
 from __future__ import annotations
 
@@ -459,10 +460,29 @@ def pin_psnr_gap(o):
     _, sse3 = o.changed_bytes(rgb, s3)
     _, sse1 = o.changed_bytes(gray, s1)
     assert sse3 == sse1 > 0
-    gap = orc.psnr(sse3, rgb.size) - orc.psnr(sse1, gray.size)
+    gap = o.psnr(sse3, rgb.size) - o.psnr(sse1, gray.size)
     assert abs(gap - 10 * math.log10(3)) < 1e-9
     # planes 1 and 2 of the stego are the cover's
     assert np.array_equal(s3.reshape(H, W, 3)[:, :, 1:], rgb[:, :, 1:])
+
+
+def pin_psnr_value(o):
+    """The absolute scale of the Section VIII measure, fixed by its
+    definition PSNR = 10 log10(255^2 / MSE), MSE = sse / n, values worked by
+    hand (the gap pin above is blind to the peak, which cancels):
+      * sse = 1 over n = 1 byte: MSE 1, so 10 log10(65025) = 20 log10(255)
+        = 48.1308036 dB (log10 255 = 2.40654018);
+      * sse = n (every byte off by one): the same 48.1308 dB for any n;
+      * sse = 650250 over n = 1000: MSE 650.25 = 65025 / 100, so 20 dB;
+      * sse = 65025 over n = 1: MSE = peak^2, so 0 dB;
+      * sse = 0: no distortion, infinite PSNR."""
+    assert abs(o.psnr(1, 1) - 48.1308036086791) < 1e-9
+    assert abs(o.psnr(786432, 786432) - 48.1308036086791) < 1e-9
+    assert abs(o.psnr(650250, 1000) - 20.0) < 1e-9
+    assert abs(o.psnr(65025, 1) - 0.0) < 1e-9
+    assert o.psnr(0, 12345) == math.inf
+    # halving the error adds 10 log10 2 dB, whatever the scale
+    assert abs(o.psnr(2, 1000) - o.psnr(4, 1000) - 10 * math.log10(2)) < 1e-9
 
 
 def pin_changed_definition(o):
@@ -619,6 +639,7 @@ PINS = [
     ("errors", pin_errors),
     ("section8_session", pin_section8_session),
     ("psnr_gap", pin_psnr_gap),
+    ("psnr_value", pin_psnr_value),
     ("changed_definition", pin_changed_definition),
     ("streamk_k1_is_stream1", pin_golden_streamk_relation),
     ("table_streamk", pin_table_streamk),

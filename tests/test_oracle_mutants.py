@@ -6,6 +6,8 @@ Each mutant is a textual substitution applied to a temporary copy of
 oracle/stego_oracle.c, compiled with gcc and loaded through ctypes.  None of
 them writes outside its buffers.
 """
+import inspect
+import math
 import os
 import shutil
 
@@ -61,6 +63,19 @@ MUTANTS = [
 ]
 
 
+# Mistakes in the Section VIII PSNR formula (oracle.psnr, Python): each is a
+# textual substitution in that function's source, compiled into a
+# replacement bound to a handle on the real oracle library.
+PSNR_MUTANTS = [
+    ("psnr_peak_256", "255.0 * 255.0", "256.0 * 256.0"),
+    ("psnr_peak_unsquared", "255.0 * 255.0 * n", "255.0 * n"),
+    ("psnr_20_log", "10.0 * math.log10", "20.0 * math.log10"),
+    ("psnr_sse_over_n_inverted", "255.0 * 255.0 * n / sse", "255.0 * 255.0 / n * sse"),
+    ("psnr_mse_per_plane", "255.0 * 255.0 * n / sse", "255.0 * 255.0 * (n / 3.0) / sse"),
+    ("psnr_natural_log", "math.log10(", "math.log("),
+]
+
+
 @pytest.fixture(scope="module")
 def workdir(tmp_path_factory):
     return tmp_path_factory.mktemp("mutants")
@@ -102,4 +117,22 @@ def test_mutant_is_caught(workdir, mname, find, repl, nth):
     o = oracle.Oracle(lib)
     caught = _first_failure(o)
     shutil.rmtree(mdir, ignore_errors=True)
+    assert caught is not None, "no pin caught mutant " + mname
+
+
+@pytest.mark.parametrize("mname,find,repl", PSNR_MUTANTS, ids=[m[0] for m in PSNR_MUTANTS])
+def test_psnr_mutant_is_caught(oracle_lib, mname, find, repl):
+    src = inspect.getsource(oracle.psnr)
+    assert find in src, "mutation site not found: " + mname
+    ns = {"math": math}
+    exec(src.replace(find, repl, 1), ns)
+    o = oracle.Oracle(oracle_lib.path)
+    o.psnr = ns["psnr"]
+    caught = None
+    for name, fn in P.PINS:
+        try:
+            fn(o)
+        except (AssertionError, ArithmeticError, ValueError):
+            caught = name
+            break
     assert caught is not None, "no pin caught mutant " + mname
