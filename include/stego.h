@@ -304,12 +304,16 @@ int stego_extract_batched(const stego_desc *d_descs, uint32_t n, stego_result *d
  * path).  The paper has no counterpart; it is stego_embed_batched with the
  * workspace taken from a scratch array inside the library instead of d_ws.
  *   n  at most STEGO_NOALLOC_MAX_DESCS; larger batches return
- *      STEGO_E_NOMEM and nothing is launched.
+ *      STEGO_E_NOMEM and nothing is launched.  Bad flags or a bad tune are
+ *      reported first (STEGO_E_INVAL), as stego_embed_batched does.
  * Other arguments, results and per-cover errors as for stego_embed_batched.
  * The scratch array (about 640 KiB) is one per GPU, held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * sets up that device (it looks up the array's device address with
  * cudaGetSymbolAddress); make that first call before any stream capture.
+ * After a cudaDeviceReset the next call sets the device up again (the
+ * address is kept per device together with the identity of the context it
+ * belongs to).
  * Every call on a device shares the one array: calls whose work overlaps on
  * the GPU (different streams, or different host threads) race and must be
  * serialised by the caller, e.g. by issuing them on one stream.  Each call
@@ -443,6 +447,29 @@ int stego_server_destroy(stego_server *s);
 #define STEGO_MEM_DEVICE 2
 #define STEGO_MEM_MANAGED 3
 int stego_pointer_kind(const void *p, int *kind, int *device_accessible);
+
+/* Test hook for the bounded device-side waits (failure detection).  The
+ * paper has no counterpart.  The shared-memory staged kernels (selected by
+ * a nonzero tile_bytes for STEGO_OP_EMBED / STEGO_OP_EXTRACT) wait on
+ * mbarriers for their bulk copies; every wait is bounded, and a CTA whose
+ * wait runs out waits for its copies still in flight, writes
+ * STEGO_E_TIMEOUT into the call's stego_result status and returns, leaving
+ * the context usable.  This call sets, for launches made after it in this
+ * process:
+ *   limit_ns          the bound of the pipeline's waits (0 = the default,
+ *                     one second; the wait for copies in flight after a
+ *                     timeout always keeps the default);
+ *   withhold_arrival  1: each stage's barrier expects one arrival more than
+ *                     the pipeline gives, so every CTA's first wait runs out
+ *                     after limit_ns (a flag that nothing sets); the CTA
+ *                     gives the missing arrival while draining, so its copies
+ *                     are still waited for.  No output byte is then written
+ *                     (the message buffer of an extract, the stego of an
+ *                     embed).  0: normal operation.
+ * On STEGO_E_TIMEOUT the outputs are otherwise unspecified (CTAs whose waits
+ * completed may have written their parts).  Returns STEGO_OK, or
+ * STEGO_E_INVAL for withhold_arrival > 1. */
+int stego_test_bounded_wait(uint64_t limit_ns, uint32_t withhold_arrival);
 
 /* Install / read the launch shape used by an operation (enum stego_op) on
  * every device.  Zero fields of `t` keep their built-in defaults.

@@ -153,6 +153,8 @@ def lib() -> ctypes.CDLL:
         L.stego_server_stats.restype = _int
         L.stego_server_destroy.argtypes = [_vp]
         L.stego_server_destroy.restype = _int
+        L.stego_test_bounded_wait.argtypes = [_u64, _u32]
+        L.stego_test_bounded_wait.restype = _int
         L.stego_set_tune.argtypes = [_int, ctypes.POINTER(Tune)]
         L.stego_set_tune.restype = _int
         L.stego_get_tune.argtypes = [_int, ctypes.POINTER(Tune)]
@@ -361,6 +363,13 @@ def stego_pointer_kind(ptr: int):
     _check(lib().stego_pointer_kind(_vp(ptr), ctypes.byref(k), ctypes.byref(a)),
            "stego_pointer_kind")
     return k.value, bool(a.value)
+
+
+def stego_test_bounded_wait(limit_ns: int, withhold_arrival: int) -> None:
+    """Bound of the staged kernels' waits and the withheld-arrival switch
+    that makes them run out (a test hook; see include/stego.h)."""
+    _check(lib().stego_test_bounded_wait(int(limit_ns), int(withhold_arrival)),
+           "stego_test_bounded_wait")
 
 
 def stego_set_tune(op: int, tune) -> None:

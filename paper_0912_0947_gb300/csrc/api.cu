@@ -4,6 +4,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "internal.cuh"
 
 namespace stego {
@@ -23,12 +25,15 @@ Shape g_shape[STEGO_OP_COUNT] = {
 };
 int g_sms[kMaxDevices];
 
-// Statistics slots: per device, the streams that own slots 0..n-1 and the
-// device address of the slot array.
+// Statistics slots: per device, the streams (by their process-unique
+// stream ID, never reused, unlike a destroyed stream's handle) that own slots
+// 0..n-1, the device address of the slot array, and the context those
+// belong to.
 constexpr int kStatSlots = 256;
-cudaStream_t g_slot_stream[kMaxDevices][kStatSlots];
+unsigned long long g_slot_sid[kMaxDevices][kStatSlots];
 int g_slot_n[kMaxDevices];
 StatSlot *g_slot_base[kMaxDevices];
+unsigned long long g_slot_ctx[kMaxDevices];
 
 struct OccEntry {
     const void *kernel;
@@ -96,6 +101,14 @@ __global__ void write_result_kernel(stego_result *res, uint64_t msg_bytes, int s
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? STEGO_OK : STEGO_E_CUDA; }
 
+// Driver entry points for the context identity, resolved through the
+// runtime so that the library does not link the driver library itself.
+using CtxGetCurrentFn = CUresult(CUDAAPI *)(CUcontext *);
+using CtxGetIdFn = CUresult(CUDAAPI *)(CUcontext, unsigned long long *);
+std::once_flag g_ctx_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
 // An image geometry that describes exactly cover_bytes bytes.
 bool geom_ok(const stego_geom *g, uint64_t cover_bytes)
 {
@@ -108,6 +121,30 @@ uint32_t bits_of(uint32_t flags) { return ((flags & STEGO_BITS_MASK) >> 8) + 1u;
 } // namespace
 
 bool tune_ok(const stego_tune *t) { return t && valid_tune_field_ranges(*t); }
+
+unsigned long long context_id()
+{
+    std::call_once(g_ctx_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id)
+        return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c || g_ctx_get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id + 1; // 0 stays "unknown"
+}
 
 Shape shape_for(int op, const stego_tune *o)
 {
@@ -199,19 +236,32 @@ StatSlot *stats_slot(cudaStream_t s)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return nullptr;
+    unsigned long long sid = 0;
+    if (cudaStreamGetId(s, &sid) != cudaSuccess)
+        return nullptr;
+    // the current context's identity: 0 when it cannot be read, and then the
+    // slots are not used (a stale device address would go unnoticed)
+    const unsigned long long ctx = context_id();
+    if (!ctx)
+        return nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_slot_base[dev]) {
+    if (g_slot_ctx[dev] != ctx) {
+        // first use on this device, or the device was reset since: the slot
+        // array was loaded afresh (zeroed) in the new context, possibly at
+        // another address, and no stream of the old context survives
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_stat_slots) != cudaSuccess || !p)
             return nullptr;
         g_slot_base[dev] = static_cast<StatSlot *>(p);
+        g_slot_n[dev] = 0;
+        g_slot_ctx[dev] = ctx;
     }
     for (int i = 0; i < g_slot_n[dev]; ++i)
-        if (g_slot_stream[dev][i] == s)
+        if (g_slot_sid[dev][i] == sid)
             return g_slot_base[dev] + i;
     if (g_slot_n[dev] == kStatSlots)
         return nullptr;
-    g_slot_stream[dev][g_slot_n[dev]] = s;
+    g_slot_sid[dev][g_slot_n[dev]] = sid;
     return g_slot_base[dev] + g_slot_n[dev]++;
 }
 

@@ -808,7 +808,8 @@ constexpr uint64_t kNoAllocBytes =
 constexpr int kNoAllocDevices = 64;
 
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoAllocDevices]; // device address of the array, per device
+void *g_noalloc_ptr[kNoAllocDevices];              // device address of the array, per device
+unsigned long long g_noalloc_ctx[kNoAllocDevices]; // the context that address belongs to
 
 } // namespace
 
@@ -819,7 +820,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 namespace {
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// per device with that device current, and again after the device was reset
+// (its context changed: the module, and with it the array, was loaded anew).
 int noalloc_scratch(void **out)
 {
     int dev = 0;
@@ -827,12 +829,15 @@ int noalloc_scratch(void **out)
         return STEGO_E_CUDA;
     if (dev < 0 || dev >= kNoAllocDevices)
         return STEGO_E_INVAL;
+    const unsigned long long ctx = stego::context_id();
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!g_noalloc_ptr[dev] || !ctx || g_noalloc_ctx[dev] != ctx) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
             return STEGO_E_CUDA;
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_ptr[dev];
     return STEGO_OK;
@@ -844,8 +849,15 @@ extern "C" int stego_embed_batched_noalloc(const stego_desc *d_descs, uint32_t n
                                            stego_result *d_results, uint32_t flags,
                                            const stego_tune *tune, void *stream)
 {
+    // argument errors first, as stego_embed_batched reports them
+    if (flags & ~(uint32_t)STEGO_FUSE_STATS)
+        return STEGO_E_INVAL;
+    if (tune && !stego::tune_ok(tune))
+        return STEGO_E_INVAL;
     if (n > kNoAllocMaxDescs)
         return STEGO_E_NOMEM;
+    if (n == 0)
+        return STEGO_OK;
     void *ws = nullptr;
     const int st = noalloc_scratch(&ws);
     if (st != STEGO_OK)

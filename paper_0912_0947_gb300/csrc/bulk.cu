@@ -20,6 +20,11 @@
 // Every wait is bounded (one second of %globaltimer).  A CTA whose wait runs
 // out stops, waits (bounded again) for the copies it still has in flight and
 // for its bulk stores, writes STEGO_E_TIMEOUT into the result and returns.
+// stego_test_bounded_wait shortens the bound and can make every CTA's first
+// wait run out (each stage's barrier then expects one arrival more than the
+// pipeline gives; the CTA gives it while draining), so that the timeout path
+// runs on demand without any fault.
+#include <atomic>
 #include <mutex>
 
 #include "s1_device.cuh"
@@ -30,6 +35,9 @@ namespace {
 constexpr int kMaxStages = 8;
 constexpr uint32_t kMaxRingBytes = 192u * 1024u;
 constexpr uint64_t kWaitNs = 1000000000ull;
+// Process-wide settings of stego_test_bounded_wait, read at each launch.
+std::atomic<uint64_t> g_wait_ns{kWaitNs};
+std::atomic<uint32_t> g_withhold{0};
 // Measured on the 201 MB full-capacity embed and extract (same box, best
 // shape of each): the embed is fastest with loads without a cache hint and
 // stores from registers (70.9 us; 72.7 us with evict-first loads, 72.7 us
@@ -61,6 +69,12 @@ __device__ __forceinline__ void mbar_init_fence()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// One plain arrival.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // One arrival that also announces `bytes` of transaction count.
 __device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes)
 {
@@ -89,8 +103,8 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Waits for the phase with the given parity to complete; false after
-// kWaitNs without completion.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// limit_ns without completion.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -98,7 +112,7 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     for (uint32_t n = 1;; ++n) {
         if (mbar_try_wait(bar, parity))
             return true;
-        if ((n & 63u) == 0 && global_ns() - t0 > kWaitNs)
+        if ((n & 63u) == 0 && global_ns() - t0 > limit_ns)
             return false;
     }
 }
@@ -200,13 +214,19 @@ __device__ __forceinline__ uint64_t local_tiles(uint64_t ntiles)
     return blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 }
 
-// After a timeout: wait (bounded) for the loads of tiles [from, issued),
-// then for the bulk stores, and report the timeout.
+// After a timeout: wait (bounded by the default limit) for the loads of
+// tiles [from, issued), then for the bulk stores, and report the timeout.
+// With `withheld`, each of those stages still lacks the arrival its barrier
+// was initialised to expect: it is given here, so the phase completes once
+// the copy's bytes have landed.
 __device__ void drain_after_timeout(const Ring &r, uint64_t from, uint64_t issued,
-                                    stego_result *res)
+                                    stego_result *res, bool withheld)
 {
+    if (withheld)
+        for (uint64_t i = from; i < issued; ++i)
+            mbar_arrive(r.bar(i));
     for (uint64_t i = from; i < issued; ++i)
-        mbar_wait(r.bar(i), r.parity(i));
+        mbar_wait(r.bar(i), r.parity(i), kWaitNs);
     bulk_wait_all();
     if (res)
         *(volatile int32_t *)&res->status = STEGO_E_TIMEOUT;
@@ -222,7 +242,8 @@ struct BulkEmbedArgs {
     uint64_t res_msg_bytes;
     StatSlot *slot;
     uint32_t stages;
-    uint32_t pad;
+    uint32_t withhold; // barriers expect one arrival the pipeline never gives
+    uint64_t wait_ns;  // bound of the pipeline's waits
 };
 
 // Stream pairs of this thread's vectors of tile i (0 past the stream).
@@ -270,7 +291,7 @@ __global__ void __launch_bounds__(512) embed_bulk(BulkEmbedArgs e)
     const uint64_t nl = local_tiles((r.nvec + r.tvec - 1) / r.tvec);
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < r.stages; ++s)
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], e.withhold ? 2u : 1u);
         mbar_init_fence();
     }
     __syncthreads();
@@ -291,7 +312,7 @@ __global__ void __launch_bounds__(512) embed_bulk(BulkEmbedArgs e)
             pc[u] = p[u];
         if (i + 1 < nl)
             tile_pairs<V>(a, r, i + 1, p); // in flight while this tile lands
-        const bool ok = mbar_wait(r.bar(i), r.parity(i));
+        const bool ok = mbar_wait(r.bar(i), r.parity(i), e.wait_ns);
         const uint64_t v0 = r.v0(i);
         if (ok) {
             uint4 *buf = reinterpret_cast<uint4 *>(r.stage(i));
@@ -335,11 +356,11 @@ __global__ void __launch_bounds__(512) embed_bulk(BulkEmbedArgs e)
     }
     if (threadIdx.x == 0) {
         if (failed)
-            drain_after_timeout(r, i, issued, e.res);
+            drain_after_timeout(r, i, issued, e.res, e.withhold != 0);
         else
             bulk_wait_all();
     }
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0 && !failed) // `failed` is the same in every thread
         s1::embed_tail<STATS>(a, changed, sse);
     if (STATS)
         block_stats(changed, sse, e.res, e.slot);
@@ -352,7 +373,8 @@ __global__ void __launch_bounds__(512) embed_bulk(BulkEmbedArgs e)
 struct BulkExtractArgs {
     s1::ExtractArgs x;
     uint32_t stages;
-    uint32_t pad;
+    uint32_t withhold; // as in BulkEmbedArgs
+    uint64_t wait_ns;
 };
 
 template <int V>
@@ -379,7 +401,7 @@ __global__ void __launch_bounds__(512) extract_bulk(BulkExtractArgs e)
     const uint64_t nl = local_tiles((r.nvec + r.tvec - 1) / r.tvec);
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < r.stages; ++s)
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], e.withhold ? 2u : 1u);
         mbar_init_fence();
     }
     __syncthreads();
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(512) extract_bulk(BulkExtractArgs e)
     uint64_t i = 0;
     bool failed = false;
     for (; i < nl; ++i) {
-        const bool ok = mbar_wait(r.bar(i), r.parity(i));
+        const bool ok = mbar_wait(r.bar(i), r.parity(i), e.wait_ns);
         if (ok) {
             const uint4 *buf = reinterpret_cast<const uint4 *>(r.stage(i));
             const uint64_t v0 = r.v0(i);
@@ -417,8 +439,8 @@ __global__ void __launch_bounds__(512) extract_bulk(BulkExtractArgs e)
             r.issue(issued++); // every thread has read stage i
     }
     if (threadIdx.x == 0 && failed)
-        drain_after_timeout(r, i, issued, e.x.res);
-    if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0)
+        drain_after_timeout(r, i, issued, e.x.res, e.withhold != 0);
+    if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0 && !failed)
         s1::extract_one(x, x.len - 1);
 }
 
@@ -431,16 +453,22 @@ int clamp_v(int v) { return (v == 1 || v == 2 || v == 8) ? v : 4; }
 std::mutex g_attr_mu;
 const void *g_attr_done[64][32]; // per device: kernels whose smem limit is raised
 int g_attr_n[64];
+unsigned long long g_attr_ctx[64]; // the context the raised limits belong to
 
 // Raises the kernel's dynamic shared memory limit to kMaxRingBytes once per
-// device.
+// device (again after a device reset, which gives the device a new context).
 cudaError_t allow_ring(const void *k)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64)
         dev = 0;
+    const unsigned long long ctx = context_id();
     std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (!ctx || g_attr_ctx[dev] != ctx) {
+        g_attr_n[dev] = 0;
+        g_attr_ctx[dev] = ctx;
+    }
     for (int i = 0; i < g_attr_n[dev]; ++i)
         if (g_attr_done[dev][i] == k)
             return cudaSuccess;
@@ -507,7 +535,8 @@ cudaError_t s1_embed_bulk(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes
     e.res_msg_bytes = res_msg_bytes;
     e.slot = stats ? slot : nullptr;
     e.stages = bulk_stages(sh);
-    e.pad = 0;
+    e.withhold = g_withhold.load(std::memory_order_relaxed);
+    e.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
     const int v = clamp_v(sh.vec);
     const void *k = stats ? embed_kernel<true>(v) : embed_kernel<false>(v);
     cudaError_t err = allow_ring(k);
@@ -535,7 +564,8 @@ cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_
     e.x.msg_even = ((uintptr_t)msg & 1u) == 0;
     e.x.res = res;
     e.stages = bulk_stages(sh);
-    e.pad = 0;
+    e.withhold = g_withhold.load(std::memory_order_relaxed);
+    e.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
     uint64_t max_len = raw_len;
     if (header) {
         const uint64_t fit = C >= 32 ? (C - 32) / 8 : 0;
@@ -556,3 +586,12 @@ cudaError_t s1_extract_bulk(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_
 }
 
 } // namespace stego
+
+extern "C" int stego_test_bounded_wait(uint64_t limit_ns, uint32_t withhold_arrival)
+{
+    if (withhold_arrival > 1u)
+        return STEGO_E_INVAL;
+    stego::g_wait_ns.store(limit_ns ? limit_ns : stego::kWaitNs, std::memory_order_relaxed);
+    stego::g_withhold.store(withhold_arrival, std::memory_order_relaxed);
+    return STEGO_OK;
+}

@@ -32,6 +32,12 @@ bool tune_ok(const stego_tune *t);
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Identity of the current CUDA context (process-unique, never reused), or 0
+// when it cannot be read.  Caches of device addresses (module globals) are
+// keyed on it: a device reset gives the device a new context, in which the
+// library's module is loaded again.
+unsigned long long context_id();
+
 // Persistent grid: min(ceil(units / units_per_cta), SMs * resident CTAs).
 // `kernel` is the __global__ function (for the occupancy query).
 int persistent_grid(const void *kernel, int threads, size_t smem, int ctas_per_sm,
@@ -78,9 +84,14 @@ struct StatSlot {
 
 // The slot of stream s on the current device, or nullptr: then the caller
 // zeroes res->changed/sse before the launch and the CTAs add into them.
+// Slots are keyed by the stream's ID (cudaStreamGetId), which the runtime
+// never reuses, so a stream created after another was destroyed never
+// shares the old stream's slot (whose last launch may still be running).
 // nullptr for streams being captured into a graph (a replay may run beside
 // direct calls on the same stream), for the per-thread default stream
-// (one handle, several streams) and once every slot is taken.
+// (one handle, several streams) and once every slot is taken (256 streams
+// per device; slots are never handed back, the later streams take the
+// zeroing path).
 StatSlot *stats_slot(cudaStream_t s);
 
 // ---------------------------------------------------------------------------

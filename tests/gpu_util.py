@@ -2,6 +2,8 @@
 both sides, chosen misalignment) and host/device transfers."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -47,3 +49,20 @@ class Guarded:
 
 def dev(a: np.ndarray, device="cuda") -> torch.Tensor:
     return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+
+
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def pmap(fn, n: int, workers: int | None = None) -> list:
+    """[fn(i) for i in range(n)] on a thread pool over every host core.  The
+    oracle's work is one C call per item, which runs without the interpreter
+    lock, so the items proceed in parallel."""
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=workers or host_threads()) as ex:
+        return list(ex.map(fn, range(n)))

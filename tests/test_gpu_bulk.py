@@ -153,3 +153,72 @@ def test_staged_8192_full_capacity(S, O, shape):
     assert r2["status"] == 0 and r2["msg_bytes"] == w.msg_bytes
     assert np.array_equal(out.cpu().numpy(), m_h)
     assert torch.equal(buf, stego)
+
+
+class withheld_arrival:
+    """Makes every staged CTA's first barrier wait run out after limit_ns
+    (each barrier expects one arrival the pipeline never gives), and
+    restores normal operation on exit."""
+
+    def __init__(self, S, limit_ns):
+        self.S, self.limit_ns = S, limit_ns
+
+    def __enter__(self):
+        self.S.stego_test_bounded_wait(self.limit_ns, 1)
+        return self
+
+    def __exit__(self, *exc):
+        self.S.stego_test_bounded_wait(0, 0)
+
+
+@pytest.mark.parametrize("shape", [(256, 4, 0, 65536), (128, 2, 2, 32768)])
+def test_bounded_wait_runs_out(S, O, shape):
+    """Failure detection without a fault: every bounded wait of the staged
+    kernels runs out (2 ms), the call reports STEGO_E_TIMEOUT in its result,
+    writes no output byte, drains its own copies, and the next normal call on
+    the same stream returns the oracle's bytes."""
+    C = 4 << 20
+    rng = np.random.default_rng(99)
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    msg = rng.integers(0, 256, C // 8 - 4 - 1001, dtype=np.uint8)  # odd length
+    st, want = O.stream1_embed(cover, msg, header=True)
+    assert st == 0
+    c = torch.from_numpy(cover).cuda()
+    m = torch.from_numpy(msg).cuda()
+    good = torch.from_numpy(want).cuda()
+    stream = torch.cuda.Stream()
+    with staged(S, shape):
+        with withheld_arrival(S, 2_000_000):
+            out = torch.full_like(c, 0x5A)
+            res = S.new_result()
+            S.stego_embed(c, out, m, S.HEADER_BE32 | S.FUSE_STATS, res, stream=stream)
+            got = torch.full((msg.size + 8,), 0xEE, dtype=torch.uint8, device="cuda")
+            res_x = S.new_result()
+            S.stego_extract(good, got, 0, S.HEADER_BE32, res_x, stream=stream)
+            stream.synchronize()
+            assert S.read_result(res)["status"] == S.E_TIMEOUT
+            assert S.read_result(res_x)["status"] == S.E_TIMEOUT
+            assert bool((out == 0x5A).all()), "a timed-out embed wrote its stego"
+            assert bool((got == 0xEE).all()), "a timed-out extract wrote its message"
+        # normal operation again, same stream
+        out = torch.full_like(c, 0x5A)
+        res = S.new_result()
+        S.stego_embed(c, out, m, S.HEADER_BE32 | S.FUSE_STATS, res, stream=stream)
+        got = torch.full((msg.size + 8,), 0xEE, dtype=torch.uint8, device="cuda")
+        res_x = S.new_result()
+        S.stego_extract(out, got, 0, S.HEADER_BE32, res_x, stream=stream)
+        stream.synchronize()
+        r = S.read_result(res)
+        assert r["status"] == 0 and (r["changed"], r["sse"]) == O.changed_bytes(cover, want)
+        assert np.array_equal(out.cpu().numpy(), want)
+        rx = S.read_result(res_x)
+        assert rx["status"] == 0 and rx["msg_bytes"] == msg.size
+        g = got.cpu().numpy()
+        assert np.array_equal(g[: msg.size], msg) and np.all(g[msg.size:] == 0xEE)
+
+
+def test_bounded_wait_argument_check(S):
+    with pytest.raises(S.StegoError) as e:
+        S.stego_test_bounded_wait(0, 2)
+    assert e.value.status == S.E_INVAL
+    S.stego_test_bounded_wait(0, 0)

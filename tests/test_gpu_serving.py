@@ -101,18 +101,25 @@ def test_alone_equals_mix(S):
     # the mix really batched and overlapped
     assert max(int(c["batch_size"]) for c in comps) > 1
     assert st["batches"] < n_req
-    # a sample against the oracle
+    # every request against the oracle: embeds byte for byte with changed
+    # and sse, extracts against the oracle's extraction of the same stego
     O = oracle.load()
-    for r in range(0, n_req, 37):
+    for r in range(n_req):
         i = int(pool.ids[r])
         c = pool.covers[i].cpu().numpy()
         msg = pool.msgs[i].cpu().numpy()
-        stt, want = O.stream1_embed(c, msg, header=True)
+        got = m_out[r].cpu().numpy()
         if pool.ops[r] == 0:
-            assert np.array_equal(m_out[r].cpu().numpy(), want)
-            assert (int(m[r]["changed"]), int(m[r]["sse"])) == O.changed_bytes(c, want)
+            stt, want = O.stream1_embed(c, msg, header=True)
+            assert stt == 0 and np.array_equal(got, want), r
+            assert (int(m[r]["changed"]), int(m[r]["sse"])) == O.changed_bytes(c, want), r
+            assert int(m[r]["msg_bytes"]) == msg.size
         else:
-            assert np.array_equal(m_out[r].cpu().numpy()[: msg.size], msg)
+            stt, want = O.stream1_extract(pool.stegos[i].cpu().numpy(), cap=msg.size + 3,
+                                          header=True)
+            assert stt == 0 and int(m[r]["msg_bytes"]) == want.size == msg.size, r
+            assert np.array_equal(got[: want.size], want), r
+            assert np.all(got[want.size:] == 0xEE), r
 
 
 def test_budget_and_bad_requests(S):

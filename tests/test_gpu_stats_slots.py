@@ -160,3 +160,40 @@ def test_graph_capture_uses_zeroing(S, O):
     torch.cuda.synchronize()
     assert (S.read_result(res2)["changed"], S.read_result(res2)["sse"]) == stats
     assert (S.read_result(res)["changed"], S.read_result(res)["sse"]) == stats
+
+
+def test_destroyed_and_recreated_streams(S, O):
+    """Streams created, given one fused-statistics embed each and destroyed
+    while that embed may still be queued or running, 300 times in a row: the
+    driver may hand a new stream the handle of a destroyed one, and each
+    embed still gets its own totals (slots are keyed by the never-reused stream
+    ID; past the 256th stream the zeroing path takes over)."""
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    cu.cuStreamCreate.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint]
+    cu.cuStreamDestroy_v2.argtypes = [ctypes.c_void_p]
+    cases = [_case(40 + i, (1 << 20) + 16 * i, fill=0.3 + 0.2 * i) for i in range(4)]
+    wants = [_want(O, c, m, {}) for c, m in cases]
+    dev = [(torch.from_numpy(c).cuda(), torch.from_numpy(m).cuda()) for c, m in cases]
+    n = 300
+    outs = [torch.empty_like(dev[i % 4][0]) for i in range(n)]
+    res = S.new_result(n=n)
+    res.fill_(-1)
+    delay_src = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    delay_dst = torch.empty_like(delay_src)
+    torch.cuda.synchronize()
+    for i in range(n):
+        h = ctypes.c_void_p()
+        assert cu.cuStreamCreate(ctypes.byref(h), 1) == 0  # non-blocking stream
+        ext = torch.cuda.ExternalStream(h.value)
+        with torch.cuda.stream(ext):
+            delay_dst.copy_(delay_src)  # keeps the embed queued past the destroy
+        c, m = dev[i % 4]
+        S.stego_embed(c, outs[i], m, S.HEADER_BE32 | S.FUSE_STATS, res[i], stream=h.value)
+        assert cu.cuStreamDestroy_v2(h) == 0
+    torch.cuda.synchronize()
+    rr = S.read_result(res)
+    for i in range(n):
+        want, stats = wants[i % 4]
+        assert rr[i]["status"] == 0 and (rr[i]["changed"], rr[i]["sse"]) == stats, i
+        assert np.array_equal(outs[i].cpu().numpy(), want), i
