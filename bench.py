@@ -13,7 +13,8 @@ traverse the cover once) / device time, summed over ranks for N > 1 (each
 rank runs its own replica; no data-path collective).
 
 Prints one JSON line.  `--impl reference` times the CPU oracle instead (on
-the host cores, rank 0 only) on a bounded prefix of the same workload.
+the host cores, rank 0 only) on the same workload, cut to a prefix only if
+the whole cover would not fit the time budget.
 """
 from __future__ import annotations
 
@@ -255,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
     if (rank == 0 or world > 1) and args.e2e_steps > 0:
-        e2e = run_e2e_pipelined(args, S, torch, dev, stream, cover, msg, C, m)
+        e2e = run_e2e_library(args, S, torch, dev, cover, msg, C, m)
         e2e["zero_copy_host_stego"] = run_e2e_zero_copy(args, S, torch, dev, stream, cover,
                                                         msg, C, m)
         e2e["explicit_copy"] = run_e2e(args, S, torch, dev, stream, cover, msg, C, m)
@@ -264,9 +265,11 @@ def run_ours(args, rank, world, local_rank):
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
                                                          "batched_video_paper2", "paper2",
                                                          "streamk", "serving", "small",
-                                                         "extract_gather"}
+                                                         "extract_gather",
+                                                         "batched_uneven_host"}
     if args.no_batched:
-        want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk"}
+        want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk",
+                 "batched_uneven_host"}
     if args.no_serving:
         want.discard("serving")
     del flush
@@ -289,6 +292,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if rank == 0 and "paper2" in want:
         legs["paper2"] = run_paper2_leg(S, AT, torch, dev, synth)
+        torch.cuda.empty_cache()
+    if rank == 0 and "batched_uneven_host" in want:
+        legs["batched_uneven_host"] = run_host_batched_leg(S, torch, dev, synth,
+                                                           count=args.uneven_count or None)
         torch.cuda.empty_cache()
     if rank == 0 and "serving" in want:
         legs["serving"] = run_serving_leg(S, AT, torch, dev, synth,
@@ -888,79 +895,151 @@ def run_e2e_zero_copy(args, S, torch, dev, stream, cover_d, msg_d, C, m):
             "h2d_bytes_per_step": 2 * C + m, "d2h_bytes_per_step": C + m + 64}
 
 
-def run_e2e_pipelined(args, S, torch, dev, stream, cover_d, msg_d, C, m, nslots=2):
-    """The step through the public API with host inputs and outputs,
-    pipelined over three streams and two device slots: host->device copies
-    of step i+1's cover and message run while step i's embed and extract
-    run on HBM and step i-1's stego and message are copied back, so both
-    link directions and the kernels overlap.  Every input byte crosses
-    host->device and every output byte device->host inside the timed
-    region."""
+def run_e2e_library(args, S, torch, dev, cover_d, msg_d, C, m, slots=3):
+    """The step through the library's host pipeline (stego_pipeline_embed):
+    every step is one host-resident job -- the cover and message are copied
+    from pinned host memory into a device slot, embedded there (fused
+    statistics), the new stego is extracted on the device (the job's
+    read-back), and the stego and the extracted message are copied back to
+    pinned host memory.  The pipeline runs neighbouring steps' copy-in,
+    kernels and copy-out at the same time on its own three streams; the
+    timed region is the whole synchronous call over all steps (host wall
+    clock), so every input and output byte crosses the link inside it."""
     cover_h = cover_d.cpu().pin_memory()
     msg_h = msg_d.cpu().pin_memory()
     stego_h = torch.empty(C, dtype=torch.uint8).pin_memory()
     out_h = torch.empty(m, dtype=torch.uint8).pin_memory()
-    res_h = torch.empty((nslots, 2, 4), dtype=torch.int64).pin_memory()
-    c_d = [torch.empty(C, dtype=torch.uint8, device=dev) for _ in range(nslots)]
-    m_d = [torch.empty(m, dtype=torch.uint8, device=dev) for _ in range(nslots)]
-    s_d = [torch.empty(C, dtype=torch.uint8, device=dev) for _ in range(nslots)]
-    o_d = [torch.empty(m, dtype=torch.uint8, device=dev) for _ in range(nslots)]
-    r_d = [S.new_result(dev, n=2) for _ in range(nslots)]  # [embed, extract]
-    s_h, s_k, s_c = (torch.cuda.Stream(dev) for _ in range(3))
-    done_h = [torch.cuda.Event() for _ in range(nslots)]
-    done_k = [torch.cuda.Event() for _ in range(nslots)]
-    done_c = [torch.cuda.Event() for _ in range(nslots)]
-    for st in (s_h, s_k, s_c):
-        st.wait_stream(stream)
-
-    def step(i):
-        j = i % nslots
-        if i >= nslots:
-            s_h.wait_event(done_k[j])  # the slot's inputs were consumed
-        with torch.cuda.stream(s_h):
-            c_d[j].copy_(cover_h, non_blocking=True)
-            m_d[j].copy_(msg_h, non_blocking=True)
-        done_h[j].record(s_h)
-        s_k.wait_event(done_h[j])
-        if i >= nslots:
-            s_k.wait_event(done_c[j])  # the slot's outputs were copied back
-        S.stego_embed(c_d[j], s_d[j], m_d[j], S.HEADER_BE32 | S.FUSE_STATS, r_d[j][0],
-                      stream=s_k)
-        S.stego_extract(s_d[j], o_d[j], 0, S.HEADER_BE32, r_d[j][1], stream=s_k)
-        done_k[j].record(s_k)
-        s_c.wait_event(done_k[j])
-        with torch.cuda.stream(s_c):
-            stego_h.copy_(s_d[j], non_blocking=True)
-            out_h.copy_(o_d[j], non_blocking=True)
-            res_h[j].copy_(r_d[j], non_blocking=True)
-        done_c[j].record(s_c)
-
-    for i in range(nslots):
-        step(i)
-    torch.cuda.synchronize(dev)
-    assert torch.equal(out_h, msg_h) and int(res_h[nslots - 1][1][2]) == m
+    # one job per slot: cover, message and read-back plus the placement slack
+    pipe = S.Pipeline(slots=slots, max_descs=1, slot_bytes=C + m + (m + 255) // 256 * 256 + 1280)
+    job = dict(cover=cover_h, stego=stego_h, msg=msg_h, readback=out_h, cover_bytes=C,
+               msg_bytes=m, flags=S.HEADER_BE32)
     n = args.e2e_steps
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s_h)
-    s_k.wait_event(e0)
-    s_c.wait_event(e0)
-    for i in range(n):
-        step(i)
-    s_h.wait_stream(s_k)
-    s_h.wait_stream(s_c)
-    e1.record(s_h)
+    jobs = S.Pipeline.jobs([job] * n)
+    res, rb = pipe.embed(S.Pipeline.jobs([job] * slots), S.FUSE_STATS, readback_results=True)
+    assert all(r["status"] == 0 for r in res + rb)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / n
+    t0 = time.perf_counter()
+    res, rb = pipe.embed(jobs, S.FUSE_STATS, readback_results=True)
+    ms = (time.perf_counter() - t0) * 1e3 / n
+    pipe.close()
+    assert all(r["status"] == 0 and r["msg_bytes"] == m for r in res + rb)
     want = torch.empty_like(cover_d)
     S.stego_embed(cover_d, want, msg_d, S.HEADER_BE32)
     torch.cuda.synchronize(dev)
     assert torch.equal(stego_h, want.cpu()), "pipelined stego differs"
-    assert torch.equal(out_h, msg_h), "pipelined message differs"
+    assert torch.equal(out_h, msg_h), "pipelined read-back differs"
     return {"value": round(2.0 * C / (ms * 1e-3) / 1e9, 2), "unit": UNIT,
             "ms_per_step": round(ms, 4), "steps": n,
-            "mode": "pipelined copies: H2D of step i+1, kernels of step i, D2H of step i-1 "
-                    "on three streams, two device slots",
-            "h2d_bytes_per_step": C + m, "d2h_bytes_per_step": C + m + 64}
+            "api": "stego_pipeline_embed (%d slots), one host job per step with a read-back "
+                   "extraction; host wall clock around the call" % slots,
+            "h2d_bytes_per_step": C + m + 72, "d2h_bytes_per_step": C + m + 64}
+
+
+def run_host_batched_leg(S, torch, dev, synth, count=None, slots=3, slot_mb=256):
+    """The 4096 uneven covers of the batched leg held in pinned host memory
+    (cover, stego and message arenas), embedded and then extracted through
+    the library's host pipeline: copy-in, batched kernels and copy-out of
+    neighbouring chunks overlapped.  Host wall clock around each call."""
+    items = synth.uneven_batch(count or 4096)
+    sizes = [it.cover_bytes for it in items]
+    mlens = [it.msg_bytes for it in items]
+    n = len(sizes)
+    off, moff, p, q = [], [], 0, 0
+    for c, m in zip(sizes, mlens):
+        off.append(p)
+        moff.append(q)
+        p += (c + 255) // 256 * 256
+        q += (m + 255) // 256 * 256
+    covers = synth.uniform_bytes(p, synth.substream(synth.SEED_BASE + 4, 1), dev).cpu()
+    covers = covers.pin_memory()
+    msgs = synth.uniform_bytes(q, synth.substream(synth.SEED_BASE + 4, 2), dev).cpu()
+    msgs = msgs.pin_memory()
+    stego = torch.empty(p, dtype=torch.uint8).pin_memory()
+    out = torch.zeros(q, dtype=torch.uint8).pin_memory()
+    cv = [covers[o:o + c] for o, c in zip(off, sizes)]
+    sv = [stego[o:o + c] for o, c in zip(off, sizes)]
+    mv = [msgs[o:o + m] for o, m in zip(moff, mlens)]
+    ov = [out[o:o + m] for o, m in zip(moff, mlens)]
+    ej = S.Pipeline.jobs([dict(cover=cv[i], stego=sv[i], msg=mv[i], cover_bytes=sizes[i],
+                               msg_bytes=mlens[i], flags=S.HEADER_BE32) for i in range(n)])
+    xj = S.Pipeline.jobs([dict(cover=sv[i], msg=ov[i], cover_bytes=sizes[i],
+                               msg_bytes=mlens[i], flags=S.HEADER_BE32) for i in range(n)])
+    modes = {}
+    for mode_name, mode in (("staged", S.PIPE_STAGED), ("auto", S.PIPE_AUTO)):
+        pipe = S.Pipeline(slots=slots, max_descs=4096, slot_bytes=slot_mb << 20, mode=mode)
+        out.zero_()
+        stego.zero_()
+        pipe.embed(ej[:64], S.FUSE_STATS)  # warm-up
+        pipe.extract(xj[:64])
+        t_e, t_x = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            re = pipe.embed(ej, S.FUSE_STATS, raw=True)
+            t_e.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            rx = pipe.extract(xj, raw=True)
+            t_x.append(time.perf_counter() - t0)
+        pipe.close()
+        re, rx = S.read_result(re), S.read_result(rx)
+        assert all(r["status"] == 0 for r in re) and all(r["status"] == 0 for r in rx)
+        assert all(rx[i]["msg_bytes"] == mlens[i] for i in range(n))
+        assert all(torch.equal(ov[i], mv[i]) for i in range(n)), "host round trip differs"
+        modes[mode_name] = (min(t_e), min(t_x))
+    # the same batch with no staging at all: the batched kernels read and
+    # write the pinned host arenas directly (zero copy)
+    stream = torch.cuda.current_stream(dev)
+    d_e = S.descs_to_device(S.pack_descs(
+        [dict(cover=cv[i], stego=sv[i], msg=mv[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]), dev)
+    d_x = S.descs_to_device(S.pack_descs(
+        [dict(cover=sv[i], msg=ov[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]), dev)
+    res_d = S.new_result(dev, n=n)
+    ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device=dev)
+    zc = {}
+    for name, fn in (("embed", lambda: S.stego_embed_batched(d_e, n, res_d, S.FUSE_STATS, ws,
+                                                             stream=stream)),
+                     ("extract", lambda: S.stego_extract_batched(d_x, n, res_d, 0, ws,
+                                                                 stream=stream))):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        zc[name + "_ms"] = round(min(ts) * 1e3, 2)
+        zc[name + "_cover_gbs"] = round(sum(sizes) / min(ts) / 1e9, 1)
+    assert all(torch.equal(ov[i], mv[i]) for i in range(n)), "zero-copy round trip differs"
+    total = sum(sizes)
+    msg_total = sum(mlens)
+    carrying = sum(8 * (m + 4) for m in mlens)
+    te, tx = modes["auto"]
+    se, sx = modes["staged"]
+    return {"workload": "4096 uneven covers (log-uniform sides 64..4096, 1 or 3 channels, "
+                        "5-100% fill) in pinned host memory",
+            "api": "stego_pipeline_embed / stego_pipeline_extract, %d slots of %d MiB, "
+                   "up to 4096 covers per chunk, automatic mode (jobs without a read-back "
+                   "are zero copy); best of 3, host wall clock" % (slots, slot_mb),
+            "covers": n, "cover_bytes": total,
+            "embed_ms": round(te * 1e3, 2), "extract_ms": round(tx * 1e3, 2),
+            "embed_cover_gbs": round(total / te / 1e9, 1),
+            "extract_cover_gbs": round(total / tx / 1e9, 1),
+            "embed_link_bytes": {"h2d": total + msg_total, "d2h": total},
+            "extract_link_bytes": {"h2d": carrying, "d2h": msg_total},
+            "staged": {"what": "every job through the slots: covers and messages copied in, "
+                               "stegos copied back by the copy engines",
+                       "embed_ms": round(se * 1e3, 2), "extract_ms": round(sx * 1e3, 2),
+                       "embed_cover_gbs": round(total / se / 1e9, 1),
+                       "extract_cover_gbs": round(total / sx / 1e9, 1),
+                       "embed_h2d_gbs": round((total + msg_total) / se / 1e9, 1),
+                       "extract_h2d_gbs": round(total / sx / 1e9, 1)},
+            "zero_copy_batched": dict(zc, api="stego_embed_batched / stego_extract_batched "
+                                              "with descriptors pointing into the pinned host "
+                                              "arenas (no staging copies); CUDA events")}
 
 
 def run_e2e(args, S, torch, dev, stream, cover_d, msg_d, C, m):
@@ -1125,7 +1204,10 @@ def run_reference(args, rank, world):
         oracle_round_trip(O, cov, msg)
     t = sum(oracle_round_trip(O, cov, msg) for _ in range(args.steps))
     value = 2.0 * sample * args.steps / t / 1e9
-    desc = ("prefix of %d bytes of the 8192x8192x3 cover with a %d-byte message "
+    whole = sample == C_full - C_full % 16
+    desc = ("the whole %d-byte 8192x8192x3 cover with a %d-byte message (full capacity) "
+            "per step" % (sample, sample // 8 - 4)) if whole else \
+           ("prefix of %d bytes of the 8192x8192x3 cover with a %d-byte message "
             "(full capacity of the prefix) per step" % (sample, sample // 8 - 4))
     return {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
@@ -1133,7 +1215,8 @@ def run_reference(args, rank, world):
         "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "single 8192x8192x3 uint8 cover, full 1-bit capacity; "
-                               "embed + extract (CPU oracle on a bounded prefix)",
+                               "embed + extract (CPU oracle, %s)" % (
+                                   "whole cover" if whole else "bounded prefix"),
                    "cover_bytes": C_full, "sample_bytes": sample},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": desc},
@@ -1169,7 +1252,8 @@ def main():
                     help="frames in the video batched leg (default 600)")
     ap.add_argument("--legs", default="",
                     help="comma list of extra legs: batched_uneven,batched_video,"
-                         "batched_video_paper2,paper2,streamk,serving,small,extract_gather, "
+                         "batched_video_paper2,paper2,streamk,serving,small,extract_gather,"
+                         "batched_uneven_host, "
                          "or none "
                          "(default all)")
     args = ap.parse_args()

@@ -430,6 +430,120 @@ int stego_server_stats(stego_server *s, uint64_t *batches, uint64_t *outstanding
  * server (not the arena). */
 int stego_server_destroy(stego_server *s);
 
+/* ------------------------------------------------------------------ */
+/* Host-resident covers: overlapped copy-in, kernels and copy-out       */
+/* ------------------------------------------------------------------ */
+/* The paper's gateway (Section V) copies the image into device memory,
+ * runs the kernel and copies the result back.  A pipeline does that for a
+ * batch of covers that live in host memory: it cuts the batch into chunks
+ * that fit one device staging slot and runs chunk k on slot k mod `slots`
+ * as three stages on three streams of its own (host -> slot copies; one
+ * batched embed in place on the slot, plus one batched extract of the new
+ * stegos for jobs that ask for a read-back, or one batched extract; slot ->
+ * host copies), so that with two or more slots the copies of neighbouring
+ * chunks in both directions overlap the kernels.  Jobs that reuse nothing
+ * on the device can instead be zero copy (see STEGO_PIPE_AUTO).  Every
+ * calculation runs in the batched kernels on the device; the host only
+ * plans the chunks and issues copies.
+ *
+ * Host buffers should be pinned (cudaHostAlloc / cudaHostRegister) for the
+ * copies to overlap.  An extraction's message is written by the kernel
+ * straight into the job's host buffer, which must therefore be memory the
+ * device may dereference (pinned and mapped, the usual case with unified
+ * addressing, or any host memory on devices with pageable memory access);
+ * otherwise that job gets STEGO_E_INVAL. */
+typedef struct stego_pipeline stego_pipeline;
+
+/* Transport of a pipeline's jobs (stego_pipeline_config.mode).
+ *   STEGO_PIPE_AUTO    jobs that reuse data on the device (an embed whose
+ *                      stego is read back) are staged through the slots;
+ *                      every other job is zero copy: the batched kernels
+ *                      read and write its host buffers over the CPU-GPU
+ *                      link (an extraction then reads only the stego's
+ *                      carrying bytes).  Zero copy needs buffers the device
+ *                      may dereference; a job whose buffers are not is
+ *                      staged.
+ *   STEGO_PIPE_STAGED  every job is staged: covers and messages copied in,
+ *                      stegos copied back, by the copy engines (extracted
+ *                      messages are still written by the kernel). */
+#define STEGO_PIPE_AUTO 0u
+#define STEGO_PIPE_STAGED 1u
+
+typedef struct stego_pipeline_config {
+    uint32_t slots;        /* device staging slots (1..8); 2 or 3 overlap   */
+    uint32_t max_descs;    /* covers per chunk (1..8192)                    */
+    uint64_t slot_bytes;   /* data bytes per slot (>= 4096) for the staged  */
+                           /* covers, messages and read-backs of a chunk    */
+    uint32_t mode;         /* STEGO_PIPE_AUTO or STEGO_PIPE_STAGED          */
+    uint32_t reserved;     /* 0                                             */
+    stego_tune tune_embed; /* launch shapes of the batched calls (zeros =   */
+    stego_tune tune_extract; /*  the installed choice)                      */
+} stego_pipeline_config;   /* 56 bytes */
+
+/* One host-resident job (host memory, 80 bytes).
+ *   cover        embed: the cover; extract: the stego image.
+ *   stego        embed: output image; may equal cover (then only the bytes
+ *                that can carry the message are copied in and back: the
+ *                first 8*|S| bytes of the stream layout, the carrying rows
+ *                of the paper layout).
+ *   msg          embed: the message (read); extract: output buffer.
+ *   readback     embed, optional (NULL = none): receives msg_bytes bytes, the
+ *                extraction of the new stego, made on the device before it
+ *                is copied back (a sender's check that the stego decodes).
+ *   cover_bytes, msg_bytes, msg_len, flags, geom  as in stego_desc. */
+typedef struct stego_host_job {
+    const uint8_t *cover;
+    uint8_t *stego;
+    uint8_t *msg;
+    uint8_t *readback;
+    uint64_t cover_bytes;
+    uint64_t msg_bytes;
+    uint64_t msg_len;
+    uint32_t flags;
+    uint32_t reserved;
+    stego_geom geom;
+} stego_host_job;
+
+/* Device arena (bytes) a pipeline with this configuration needs: per slot
+ * its descriptors, results, batched workspace and data area.  0 for an
+ * invalid configuration. */
+uint64_t stego_pipeline_arena_bytes(const stego_pipeline_config *cfg);
+
+/* Creates a pipeline on the current device.  d_arena: caller-owned device
+ * memory of arena_bytes >= stego_pipeline_arena_bytes(cfg), 256-byte
+ * aligned, used until stego_pipeline_destroy.  The pipeline allocates no
+ * device memory; it creates three streams and allocates pinned host staging
+ * for descriptors and results here.  One call at a time per pipeline. */
+int stego_pipeline_create(const stego_pipeline_config *cfg, void *d_arena, uint64_t arena_bytes,
+                          stego_pipeline **out);
+
+/* Embeds jobs[0..n) (host array) and returns when every output is in host
+ * memory.  results (host, n): per job, as stego_embed_batched's results.
+ * readback_results (host, n, optional): per job the read-back extraction's
+ * result (zeros for jobs without a read-back); on a read-back error the
+ * readback buffer's contents are unspecified.  flags: STEGO_FUSE_STATS or 0.
+ * Per-job argument errors (those of stego_embed_batched, plus
+ * STEGO_E_NOMEM for a job that does not fit one slot: it needs cover_bytes
+ * + msg_bytes + 1280 bytes, plus msg_bytes rounded up to 256 with a
+ * read-back; an extraction needs cover_bytes + 768) are that job's status;
+ * its stego is not written and the other jobs proceed.  Returns STEGO_OK,
+ * STEGO_E_INVAL or STEGO_E_CUDA (then outputs and results are
+ * unspecified). */
+int stego_pipeline_embed(stego_pipeline *p, const stego_host_job *jobs, uint32_t n,
+                         stego_result *results, stego_result *readback_results, uint32_t flags);
+
+/* Extracts jobs[0..n) (host array; cover = the stego image, msg = output of
+ * msg_bytes capacity) and returns when every message is in host memory;
+ * results as stego_extract_batched's (STEGO_E_NOMEM for a job that does not
+ * fit one slot).  Device-detected errors (header) leave that job's message
+ * buffer unwritten. */
+int stego_pipeline_extract(stego_pipeline *p, const stego_host_job *jobs, uint32_t n,
+                           stego_result *results);
+
+/* Waits for the pipeline's streams, destroys them and frees its host
+ * staging (not the arena). */
+int stego_pipeline_destroy(stego_pipeline *p);
+
 /* Where a buffer lives, as the CUDA runtime of the current device reports
  * it, and whether this library's kernels may read and write it directly.
  *   *kind: STEGO_MEM_PAGEABLE (ordinary host memory), STEGO_MEM_PINNED

@@ -78,6 +78,25 @@ class ServerConfig(ctypes.Structure):
                 ("tune_extract", Tune)]
 
 
+PIPE_AUTO, PIPE_STAGED = 0, 1
+
+
+class PipelineConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_descs", ctypes.c_uint32),
+                ("slot_bytes", ctypes.c_uint64), ("mode", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("tune_embed", Tune),
+                ("tune_extract", Tune)]
+
+
+# stego_host_job as laid out in host memory (80 bytes)
+HOST_JOB_DTYPE = np.dtype([
+    ("cover", "<u8"), ("stego", "<u8"), ("msg", "<u8"), ("readback", "<u8"),
+    ("cover_bytes", "<u8"), ("msg_bytes", "<u8"), ("msg_len", "<u8"),
+    ("flags", "<u4"), ("reserved", "<u4"),
+    ("width", "<u4"), ("height", "<u4"), ("channels", "<u4"), ("plane", "<u4"),
+])
+assert HOST_JOB_DTYPE.itemsize == 80
+
 # stego_request / stego_completion as laid out in host memory (64 bytes each)
 REQUEST_DTYPE = np.dtype([
     ("op", "<u4"), ("flags", "<u4"), ("cover", "<u8"), ("stego", "<u8"), ("msg", "<u8"),
@@ -153,6 +172,17 @@ def lib() -> ctypes.CDLL:
         L.stego_server_stats.restype = _int
         L.stego_server_destroy.argtypes = [_vp]
         L.stego_server_destroy.restype = _int
+        L.stego_pipeline_arena_bytes.argtypes = [ctypes.POINTER(PipelineConfig)]
+        L.stego_pipeline_arena_bytes.restype = _u64
+        L.stego_pipeline_create.argtypes = [ctypes.POINTER(PipelineConfig), _vp, _u64,
+                                            ctypes.POINTER(_vp)]
+        L.stego_pipeline_create.restype = _int
+        L.stego_pipeline_embed.argtypes = [_vp, _vp, _u32, _vp, _vp, _u32]
+        L.stego_pipeline_embed.restype = _int
+        L.stego_pipeline_extract.argtypes = [_vp, _vp, _u32, _vp]
+        L.stego_pipeline_extract.restype = _int
+        L.stego_pipeline_destroy.argtypes = [_vp]
+        L.stego_pipeline_destroy.restype = _int
         L.stego_test_bounded_wait.argtypes = [_u64, _u32]
         L.stego_test_bounded_wait.restype = _int
         L.stego_set_tune.argtypes = [_int, ctypes.POINTER(Tune)]
@@ -240,9 +270,10 @@ def new_result(device="cuda", n: int | None = None) -> torch.Tensor:
     return torch.zeros(shape, dtype=torch.int64, device=device)
 
 
-def read_result(res: torch.Tensor) -> dict | list[dict]:
-    """Host view of stego_result(s): changed, sse, msg_bytes, status."""
-    a = res.detach().cpu().numpy()
+def read_result(res) -> dict | list[dict]:
+    """Host view of stego_result(s) (a tensor or an int64 numpy array):
+    changed, sse, msg_bytes, status."""
+    a = res.detach().cpu().numpy() if isinstance(res, torch.Tensor) else np.asarray(res)
     one = a.ndim == 1
     a = a.reshape(-1, RESULT_WORDS)
     out = []
@@ -501,6 +532,92 @@ class Server:
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().stego_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# -- host-resident covers: the overlapped copy pipeline ----------------------------
+
+def _host_ptr(t, what: str):
+    """Address of a contiguous uint8 CPU tensor (pinned for the copies to
+    overlap) or None."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError("%s must be a CPU tensor (host memory)" % what)
+    if t.dtype != torch.uint8 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous uint8 tensor" % what)
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+class Pipeline:
+    """A stego_pipeline: embed / extract batches of covers held in host
+    memory, with host->device copies, kernels and device->host copies of
+    neighbouring chunks overlapped (include/stego.h).  The device arena is
+    a torch tensor owned here."""
+
+    def __init__(self, slots: int = 2, max_descs: int = 1024, slot_bytes: int = 256 << 20,
+                 mode: int = PIPE_AUTO, tune_embed=(0, 0, 0, 0), tune_extract=(0, 0, 0, 0),
+                 device="cuda"):
+        cfg = PipelineConfig(int(slots), int(max_descs), int(slot_bytes), int(mode), 0,
+                             Tune(*tune_embed), Tune(*tune_extract))
+        n = int(lib().stego_pipeline_arena_bytes(ctypes.byref(cfg)))
+        if n == 0:
+            raise StegoError(E_INVAL, "stego_pipeline_arena_bytes")
+        self.arena = torch.empty(n, dtype=torch.uint8, device=device)
+        h = _vp(0)
+        _check(lib().stego_pipeline_create(ctypes.byref(cfg), self.arena.data_ptr(), n,
+                                           ctypes.byref(h)), "stego_pipeline_create")
+        self._h = h
+        self.cfg = cfg
+
+    @staticmethod
+    def jobs(items) -> np.ndarray:
+        """Pack dicts (keys of HOST_JOB_DTYPE; CPU tensors allowed for cover,
+        stego, msg, readback) into a host array of stego_host_job records."""
+        a = np.zeros(len(items), dtype=HOST_JOB_DTYPE)
+        for i, it in enumerate(items):
+            for k, v in it.items():
+                if isinstance(v, torch.Tensor):
+                    v = _host_ptr(v, k)
+                a[i][k] = 0 if v is None else v
+        return a
+
+    def embed(self, jobs: np.ndarray, flags: int = FUSE_STATS, readback_results: bool = False,
+              raw: bool = False):
+        """Results (list of dicts; with raw, the int64 [n, 4] array of
+        stego_result records) and, with readback_results, the read-back
+        extractions' results too."""
+        jobs = np.ascontiguousarray(jobs, dtype=HOST_JOB_DTYPE)
+        n = len(jobs)
+        res = np.zeros((max(n, 1), RESULT_WORDS), dtype=np.int64)
+        rb = np.zeros((max(n, 1), RESULT_WORDS), dtype=np.int64) if readback_results else None
+        _check(lib().stego_pipeline_embed(self._h, jobs.ctypes.data, n, res.ctypes.data,
+                                          rb.ctypes.data if rb is not None else None,
+                                          int(flags)), "stego_pipeline_embed")
+        conv = (lambda a: a[:n]) if raw else (lambda a: read_result(a[:n]) if n else [])
+        if readback_results:
+            return conv(res), conv(rb)
+        return conv(res)
+
+    def extract(self, jobs: np.ndarray, raw: bool = False):
+        jobs = np.ascontiguousarray(jobs, dtype=HOST_JOB_DTYPE)
+        n = len(jobs)
+        res = np.zeros((max(n, 1), RESULT_WORDS), dtype=np.int64)
+        _check(lib().stego_pipeline_extract(self._h, jobs.ctypes.data, n, res.ctypes.data),
+               "stego_pipeline_extract")
+        if raw:
+            return res[:n]
+        return read_result(res[:n]) if n else []
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().stego_pipeline_destroy(self._h)
         self._h = None
 
     def __del__(self):

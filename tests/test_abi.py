@@ -162,3 +162,27 @@ def test_capacity_is_the_oracles_boundary(built):
         st, _ = O.paper2_embed(cover, W, H, ch, plane,
                                rng.integers(0, 256, cap + 1, dtype=np.uint8))
         assert st != oracle.OK
+
+
+def test_host_job_packing():
+    """stego_host_job records (80 bytes) packed from CPU tensors: pointers,
+    sizes, flags and geometry land in their fields; None is a null pointer."""
+    import numpy as np
+    import torch
+
+    import paper_0912_0947_gb300 as S
+    c = torch.zeros(100, dtype=torch.uint8)
+    m = torch.zeros(7, dtype=torch.uint8)
+    a = S.Pipeline.jobs([dict(cover=c, stego=c, msg=m, readback=None, cover_bytes=100,
+                              msg_bytes=7, msg_len=3, flags=S.LAYOUT_PAPER2, width=10,
+                              height=5, channels=2, plane=1)])
+    assert a.dtype.itemsize == 80
+    r = a[0]
+    assert r["cover"] == r["stego"] == c.data_ptr() and r["msg"] == m.data_ptr()
+    assert r["readback"] == 0
+    assert (r["cover_bytes"], r["msg_bytes"], r["msg_len"]) == (100, 7, 3)
+    assert (r["flags"], r["width"], r["height"], r["channels"], r["plane"]) == (1, 10, 5, 2, 1)
+    raw = a.view(np.uint64)  # the pointer and size words in C order
+    assert int(raw[0]) == c.data_ptr() and int(raw[4]) == 100
+    with pytest.raises(TypeError):  # device tensors are not host buffers
+        S.Pipeline.jobs([dict(cover=torch.zeros(4, dtype=torch.uint8, device="meta"))])
