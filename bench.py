@@ -42,6 +42,11 @@ FALLBACK_HBM_GBS = 6800.0
 # Writes still dirty in the L2 when the kernel exits are not in the count.
 NCU_TRAFFIC = {"embed_vec": {"src_sha": "b72ea941b4dfa871", "bytes": 226528512 + 144812288},
                "embed_bulk": {"src_sha": "c5b02751867fd4e8", "bytes": 226599680 + 142849024}}
+# The same counters for one launch in the middle of the steady-state
+# sequence (back-to-back launches over distinct buffers, no flush): the
+# previous launches' deferred write-backs land in it as its own do in the
+# next ones, so it counts about one launch's full traffic.
+NCU_TRAFFIC_STEADY = {}
 KERNEL_SOURCES = ("s1_device.cuh", "stream1.cu", "bulk.cu", "internal.cuh")
 MAX_RING = 192 * 1024
 
@@ -201,6 +206,12 @@ def run_ours(args, rank, world, local_rank):
                             "best_register_us": round(min(t for s_, t in table if not s_[3]), 2),
                             "best_staged_us": round(min(staged), 2) if staged else None}
 
+    if args.steady_only:
+        return {"steady_only": run_steady_leg(S, torch, dev, stream, cover, msg, C, m,
+                                              max(args.steady_pairs, 2)),
+                "launch": {"embed": tune_dict(S.stego_get_tune(S.OP_EMBED)),
+                           "extract": tune_dict(S.stego_get_tune(S.OP_EXTRACT))}}
+
     def step(ev=None):
         flush()
         if ev:
@@ -253,6 +264,11 @@ def run_ours(args, rank, world, local_rank):
         copy = {"what": "torch copy_ of the %d-byte cover into the stego buffer (2C bytes), "
                         "L2 flushed, median of 20" % C,
                 "us": round(t_copy, 2), "gbs": round(copy_gbs, 1)}
+    # ---- steady state: back-to-back launches over distinct buffers ----------
+    steady = None
+    if rank == 0 and args.steady_pairs > 0:
+        steady = run_steady_leg(S, torch, dev, stream, cover, msg, C, m, args.steady_pairs)
+        torch.cuda.empty_cache()
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
     if (rank == 0 or world > 1) and args.e2e_steps > 0:
@@ -266,10 +282,11 @@ def run_ours(args, rank, world, local_rank):
                                                          "batched_video_paper2", "paper2",
                                                          "streamk", "serving", "small",
                                                          "extract_gather",
-                                                         "batched_uneven_host"}
+                                                         "batched_uneven_host",
+                                                         "batched_uneven_misaligned"}
     if args.no_batched:
         want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk",
-                 "batched_uneven_host"}
+                 "batched_uneven_host", "batched_uneven_misaligned"}
     if args.no_serving:
         want.discard("serving")
     del flush
@@ -292,6 +309,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if rank == 0 and "paper2" in want:
         legs["paper2"] = run_paper2_leg(S, AT, torch, dev, synth)
+        torch.cuda.empty_cache()
+    if rank == 0 and "batched_uneven_misaligned" in want:
+        legs["batched_uneven_misaligned"] = run_misaligned_batched_leg(
+            S, AT, torch, dev, stream, synth, count=args.uneven_count or None)
         torch.cuda.empty_cache()
     if rank == 0 and "batched_uneven_host" in want:
         legs["batched_uneven_host"] = run_host_batched_leg(S, torch, dev, synth,
@@ -357,6 +378,10 @@ def run_ours(args, rank, world, local_rank):
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic,
+                     "regime": "L2 flushed before the launch, write-back deferred: stego "
+                               "lines still dirty in the L2 when the kernel ends reach DRAM "
+                               "after the timed interval (the ncu traffic counts only what "
+                               "was written back during the launch)",
                      "note": "achieved = (2C + T/8) bytes / mean event time of the stego_embed "
                              "call (one kernel launch: the statistics go through the "
                              "stream's accumulator slot, no zeroing copy)"},
@@ -370,6 +395,17 @@ def run_ours(args, rank, world, local_rank):
         "wall_ms_per_step_incl_flush": round(t_wall * 1e3 / args.steps, 4),
         "clocks": clocks,
     }
+    if steady:
+        st_emb = emb_bytes / (steady["embed_us"] * 1e-6) / 1e9
+        st_ext = ext_bytes / (steady["extract_us"] * 1e-6) / 1e9
+        rec_s = NCU_TRAFFIC_STEADY.get(fam)
+        line["roofline"].update({
+            "achieved_steady": round(st_emb, 1), "frac_steady": round(st_emb / peak, 4),
+            "traffic_steady": rec_s["bytes"] if rec_s and rec_s["src_sha"] == sha else None,
+            "steady": dict(steady, embed_frac=round(st_emb / peak, 4),
+                           extract_frac=round(st_ext / peak, 4),
+                           regime="steady state: back-to-back launches, every write-back "
+                                  "inside the timed interval")})
     if e2e:
         line["e2e"] = e2e
     line.update(legs)
@@ -559,6 +595,94 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
         "outputs_identical": same,
         **extra,
     }
+
+
+def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None):
+    """The 4096-cover uneven batch with every cover 1..15 bytes past a
+    16-byte boundary and every stego at its own random offset (the funnel
+    routine: stego vectors joined from cover vector pairs; same offsets take
+    the shift routine), messages at random parity, against the same batch in
+    256-byte aligned slots; outputs compared with the aligned batch's."""
+    items = synth.uneven_batch(count or 4096)
+    sizes = [it.cover_bytes for it in items]
+    mlens = [it.msg_bytes for it in items]
+    n = len(sizes)
+    import numpy as np
+    rng = np.random.default_rng(7)
+    coff = [int(x) for x in rng.integers(1, 16, n)]
+    soff = [int(x) for x in rng.integers(1, 16, n)]
+    moff = [int(x) for x in rng.integers(0, 2, n)]
+
+    def layout(offs, lens, pad):
+        pos, p = [], 0
+        for o, c in zip(offs, lens):
+            pos.append(p + o)
+            p += (c + pad + 255) // 256 * 256
+        return pos, p
+
+    cpos, pc = layout(coff, sizes, 16)
+    spos, ps = layout(soff, sizes, 16)
+    mpos, pm = layout(moff, mlens, 2)
+    apos, pa = layout([0] * n, sizes, 0)
+    bpos, pb = layout([0] * n, mlens, 0)
+    covers = torch.empty(pc, dtype=torch.uint8, device=dev)
+    msgs = torch.empty(pm, dtype=torch.uint8, device=dev)
+    acov = synth.uniform_bytes(pa, synth.substream(synth.SEED_BASE + 4, 1), dev)
+    amsg = synth.uniform_bytes(pb, synth.substream(synth.SEED_BASE + 4, 2), dev)
+    for i in range(n):
+        covers[cpos[i]:cpos[i] + sizes[i]] = acov[apos[i]:apos[i] + sizes[i]]
+        msgs[mpos[i]:mpos[i] + mlens[i]] = amsg[bpos[i]:bpos[i] + mlens[i]]
+    stego = torch.empty(ps, dtype=torch.uint8, device=dev)
+    astego = torch.empty_like(acov)
+    out = torch.empty(pm, dtype=torch.uint8, device=dev)
+    aout = torch.empty_like(amsg)
+    cv = [covers[cpos[i]:cpos[i] + sizes[i]] for i in range(n)]
+    sv = [stego[spos[i]:spos[i] + sizes[i]] for i in range(n)]
+    mv = [msgs[mpos[i]:mpos[i] + mlens[i]] for i in range(n)]
+    ov = [out[mpos[i]:mpos[i] + mlens[i]] for i in range(n)]
+    acv = [acov[apos[i]:apos[i] + sizes[i]] for i in range(n)]
+    asv = [astego[apos[i]:apos[i] + sizes[i]] for i in range(n)]
+    amv = [amsg[bpos[i]:bpos[i] + mlens[i]] for i in range(n)]
+    aov = [aout[bpos[i]:bpos[i] + mlens[i]] for i in range(n)]
+    pk = lambda c, s_, m_: S.descs_to_device(S.pack_descs(
+        [dict(cover=c[i], stego=s_[i], msg=m_[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]), dev)
+    px = lambda st_, o_: S.descs_to_device(S.pack_descs(
+        [dict(cover=st_[i], msg=o_[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]), dev)
+    d_me, d_mx = pk(cv, sv, mv), px(sv, ov)
+    d_ae, d_ax = pk(acv, asv, amv), px(asv, aov)
+    res = S.new_result(dev, n=n)
+    ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device=dev)
+    flush = AT.Flusher(dev)
+    emb = lambda d: S.stego_embed_batched(d, n, res, S.FUSE_STATS, ws, stream=stream)
+    ext = lambda d: S.stego_extract_batched(d, n, res, 0, ws, stream=stream)
+    t = {"misaligned_embed_us": AT.time_call(lambda: emb(d_me), flush, 7),
+         "aligned_embed_us": AT.time_call(lambda: emb(d_ae), flush, 7),
+         "misaligned_extract_us": AT.time_call(lambda: ext(d_mx), flush, 7),
+         "aligned_extract_us": AT.time_call(lambda: ext(d_ax), flush, 7)}
+    torch.cuda.synchronize(dev)
+    same = all(torch.equal(sv[i], asv[i]) and torch.equal(ov[i], mv[i]) for i in range(n))
+    assert same, "misaligned batched outputs differ from the aligned batch's"
+    total = sum(sizes)
+    T = [8 * (m + 4) for m in mlens]
+    emb_bytes = sum(2 * c + t_ // 8 for c, t_ in zip(sizes, T))
+    ext_bytes = sum(t_ + t_ // 8 for t_ in T)
+    peak, _ = hbm_peak()
+    frac = lambda b, us: round(b / (us * 1e-6) / 1e9 / peak, 4)
+    return {"workload": "4096 uneven covers as in batched_uneven, each cover 1..15 bytes past "
+                        "a 16-byte boundary, each stego at its own random offset 1..15, "
+                        "messages at random parity",
+            "covers": n, "cover_bytes": total,
+            **{k: round(v, 1) for k, v in t.items()},
+            "hbm_frac": {"misaligned_embed": frac(emb_bytes, t["misaligned_embed_us"]),
+                         "aligned_embed": frac(emb_bytes, t["aligned_embed_us"]),
+                         "misaligned_extract": frac(ext_bytes, t["misaligned_extract_us"]),
+                         "aligned_extract": frac(ext_bytes, t["aligned_extract_us"])},
+            "misaligned_over_aligned": {
+                "embed": round(t["misaligned_embed_us"] / t["aligned_embed_us"], 3),
+                "extract": round(t["misaligned_extract_us"] / t["aligned_extract_us"], 3)},
+            "outputs_identical_to_aligned": same}
 
 
 def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds=1.0):
@@ -851,6 +975,48 @@ def run_small_leg(S, AT, torch, dev, synth, reps=25, burst=1000):
     assert torch.equal(out, msg)
     r["graph_embed_extract_us"] = round(e0.elapsed_time(e1) * 1e3 / burst, 2)
     return r
+
+
+def run_steady_leg(S, torch, dev, stream, cover, msg, C, m, pairs, rounds=5):
+    """The timed embed and extract launched back to back, with no flush in
+    between, over `pairs` distinct cover/stego/message sets (pairs x 427 MB,
+    far more than the 129 MB L2): each launch's stego writes that are still
+    dirty in the L2 when it ends are written back while the next launches
+    run, inside the timed interval, so the mean launch time is the steady
+    state.  One event interval around all pairs x rounds launches."""
+    covers = [cover.clone() for _ in range(pairs)]
+    msgs = [msg.clone() for _ in range(pairs)]
+    stegos = [torch.empty_like(cover) for _ in range(pairs)]
+    outs = [torch.empty_like(msg) for _ in range(pairs)]
+    res = S.new_result(dev, n=pairs)
+    fe, fx = S.HEADER_BE32 | S.FUSE_STATS, S.HEADER_BE32
+
+    def emb(k):
+        S.stego_embed(covers[k], stegos[k], msgs[k], fe, res[k], stream=stream)
+
+    def ext(k):
+        S.stego_extract(stegos[k], outs[k], 0, fx, res[k], stream=stream)
+
+    out = {}
+    for name, fn in (("embed", emb), ("extract", ext)):
+        for k in range(pairs):  # warm-up, and the stegos for the extract
+            fn(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(rounds):
+            for k in range(pairs):
+                fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name + "_us"] = round(e0.elapsed_time(e1) * 1e3 / (rounds * pairs), 2)
+    rr = S.read_result(res)
+    assert all(r["status"] == 0 and r["msg_bytes"] == m for r in rr)
+    assert all(torch.equal(o, msg) for o in outs), "steady-state round trip differs"
+    out.update({"pairs": pairs, "launches": rounds * pairs,
+                "what": "back-to-back launches over %d distinct 8192x8192x3 cover/stego/message "
+                        "sets (%.1f GB), no flush between them; one event interval" % (
+                            pairs, pairs * (2 * C + m) / 1e9)})
+    return out
 
 
 def tune_dict(t):
@@ -1232,6 +1398,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--steady-pairs", type=int, default=6,
+                    help="distinct cover/stego sets of the steady-state leg (0: skip)")
+    ap.add_argument("--steady-only", action="store_true",
+                    help="run only the steady-state sequence (for an ncu capture)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1253,7 +1423,7 @@ def main():
     ap.add_argument("--legs", default="",
                     help="comma list of extra legs: batched_uneven,batched_video,"
                          "batched_video_paper2,paper2,streamk,serving,small,extract_gather,"
-                         "batched_uneven_host, "
+                         "batched_uneven_host,batched_uneven_misaligned, "
                          "or none "
                          "(default all)")
     args = ap.parse_args()

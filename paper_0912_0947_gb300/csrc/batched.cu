@@ -5,7 +5,7 @@
 // a batch is cut into fixed-size tiles that one persistent grid claims from
 // a work counter.
 //
-// Per call, three stream-ordered launches (all capturable in a CUDA graph):
+// Per call, stream-ordered launches (all capturable in a CUDA graph):
 //   1. prep      one thread per descriptor: validate it, (extract) read its
 //                32-bit header, write its result and its tile count;
 //   2. scan      one CTA: exclusive scan of the tile counts into tile
@@ -15,10 +15,14 @@
 //                current chunk is processed), find the owning descriptor by
 //                binary search over the offsets once per chunk, and run the
 //                same per-vector code as the single-cover kernels on each
-//                tile.
+//                tile; one persistent kernel per tile space (one-bit stream
+//                on 16-byte aligned buffers, one-bit stream on misaligned
+//                buffers, paper layout), each exiting at once when its space
+//                is empty.
 // Workspace (caller-owned scratch, 16-byte aligned):
-//   [0, 64)                 head: total tiles, work counter
-//   [64, 64 + 8(n+1))       tile offsets (counts before the scan)
+//   [0, 64)                 head: tile totals and work counters
+//   [64, 64 + 24(n+1))      tile offsets of the three spaces (counts before
+//                           the scan)
 //   [info_off, +64n)        per-descriptor derived sizes, geometry and mode
 // Both layouts batch: the one-bit stream in tiles of cover bytes; the
 // paper's layout (Sections VI/VII) in tiles of whole rows (copy, barrier,
@@ -37,11 +41,13 @@ namespace stego {
 namespace {
 
 struct WsHead {
-    unsigned long long total;     // one-bit stream tiles
+    unsigned long long total;     // one-bit stream tiles, aligned buffers
     unsigned long long counter;
     unsigned long long total_p;   // paper-layout tiles
     unsigned long long counter_p;
-    unsigned long long pad[4];
+    unsigned long long total_m;   // one-bit stream tiles, misaligned buffers
+    unsigned long long counter_m;
+    unsigned long long pad[2];
 };
 
 struct DescInfo {
@@ -49,9 +55,10 @@ struct DescInfo {
     uint64_t t_bytes; // stream embed: carrying bytes
     uint64_t len;     // stream embed: stream bytes; extract / paper: message bytes
     uint32_t nbits;   // header value
-    uint32_t bits;    // kHeader | kVec | kMsgEven
-    uint32_t W, H;    // paper layout geometry
-    uint32_t channels, plane;
+    uint32_t bits;    // kHeader | kVec | kMsgEven | kFunnel
+    uint32_t W, H;    // paper layout geometry; misaligned stream: head bytes,
+                      // funnel byte selector
+    uint32_t channels, plane; // misaligned stream embed: channels = Q (funnel word offset)
     uint32_t mode;     // paper layout: one of the kP2* work kinds
     uint32_t per_tile; // paper layout: units, rows or runs per tile
     uint32_t pad[2];
@@ -59,23 +66,29 @@ struct DescInfo {
 static_assert(sizeof(DescInfo) == 64, "DescInfo is 64 bytes");
 
 constexpr uint32_t kHeader = 1u, kVec = 2u, kMsgEven = 4u;
+// misaligned stream embed: cover and stego at different addresses mod 16
+// (stego vectors joined from cover vector pairs); otherwise the same
+// misalignment (vectors after a scalar head)
+constexpr uint32_t kFunnel = 8u;
 // paper-layout work kinds (0 = the one-bit stream layout)
 constexpr uint32_t kP2Units = 1u, kP2RowsCopy = 2u, kP2Rows = 3u, kP2Runs = 4u, kP2RowsX = 5u,
                    kP2UnitsInPlace = 6u;
 constexpr uint32_t kChunk = 4u; // tiles per claim
 
-// Workspace: head (64 B), stream tile offsets (n+1), paper tile offsets
-// (n+1), per-descriptor info (64 B each, 16-byte aligned).
+// Workspace: head (64 B), aligned-stream, paper and misaligned-stream tile
+// offsets (n+1 each), per-descriptor info (64 B each, 16-byte aligned).
 constexpr uint64_t startp_off(uint32_t n) { return 64ull + 8ull * ((uint64_t)n + 1); }
+constexpr uint64_t startm_off(uint32_t n) { return 64ull + 16ull * ((uint64_t)n + 1); }
 constexpr uint64_t info_off(uint32_t n)
 {
-    return (64ull + 16ull * ((uint64_t)n + 1) + 15ull) & ~15ull;
+    return (64ull + 24ull * ((uint64_t)n + 1) + 15ull) & ~15ull;
 }
 
 struct WsView {
     WsHead *head;
-    unsigned long long *start;   // stream-layout tile offsets
+    unsigned long long *start;   // stream-layout tile offsets, aligned buffers
     unsigned long long *start_p; // paper-layout tile offsets
+    unsigned long long *start_m; // stream-layout tile offsets, misaligned buffers
     DescInfo *info;
 };
 
@@ -85,6 +98,7 @@ WsView ws_view(void *ws, uint32_t n)
     v.head = reinterpret_cast<WsHead *>(ws);
     v.start = reinterpret_cast<unsigned long long *>((char *)ws + 64);
     v.start_p = reinterpret_cast<unsigned long long *>((char *)ws + startp_off(n));
+    v.start_m = reinterpret_cast<unsigned long long *>((char *)ws + startm_off(n));
     v.info = reinterpret_cast<DescInfo *>((char *)ws + info_off(n));
     return v;
 }
@@ -221,10 +235,45 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
                        ((d_aligned16(D.cover) && d_aligned16(D.stego)) ? kVec : 0u) |
                        ((((uintptr_t)D.msg & 1u) == 0) ? kMsgEven : 0u);
             tiles = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
+            if (!(inf.bits & kVec)) {
+                // misaligned: aligned vectors after h head bytes, in tiles
+                // of tile_bytes/16 vectors, when at least one vector fits
+                const uint32_t hc = (uint32_t)((16u - ((uintptr_t)D.cover & 15u)) & 15u);
+                const uint32_t hs = (uint32_t)((16u - ((uintptr_t)D.stego & 15u)) & 15u);
+                const bool same = (((uintptr_t)D.cover ^ (uintptr_t)D.stego) & 15u) == 0;
+                const uint32_t h = same ? hc : hs;
+                if ((same || !inplace) && inf.n_bytes >= (uint64_t)h + 16u) {
+                    const uint64_t nvb = (inf.n_bytes - h) >> 4;
+                    const uint64_t tv = tile_bytes / 16u;
+                    inf.W = h;
+                    if (!same) {
+                        const uint32_t dd = (uint32_t)(((uintptr_t)D.cover + hs) & 15u);
+                        const uint32_t b = dd & 3u;
+                        inf.bits |= kFunnel;
+                        inf.H = b | ((b + 1) << 4) | ((b + 2) << 8) | ((b + 3) << 12);
+                        inf.channels = dd >> 2;
+                    }
+                    inf.per_tile = (uint32_t)tv;
+                    inf.mode = 0;
+                    ws.info[d] = inf;
+                    ws.start[d] = 0ull;
+                    ws.start_p[d] = 0ull;
+                    ws.start_m[d] = (nvb + tv - 1) / tv;
+                    stego_result r;
+                    r.changed = 0;
+                    r.sse = 0;
+                    r.msg_bytes = D.msg_bytes;
+                    r.status = STEGO_OK;
+                    r.reserved = 0;
+                    results[d] = r;
+                    continue;
+                }
+            }
         }
         ws.info[d] = inf;
         ws.start[d] = inf.mode ? 0ull : tiles;
         ws.start_p[d] = inf.mode ? tiles : 0ull;
+        ws.start_m[d] = 0ull;
         stego_result r;
         r.changed = 0;
         r.sse = 0;
@@ -308,13 +357,33 @@ __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *
             inf.len = len;
             inf.n_bytes = 8u * len;
             inf.nbits = nbits;
-            inf.bits = (header ? kHeader : 0u) | (d_aligned16(D.cover) ? kVec : 0u) |
+            const uint8_t *carrying = D.cover + (header ? 32u : 0u);
+            inf.bits = (header ? kHeader : 0u) | (d_aligned16(carrying) ? kVec : 0u) |
                        ((((uintptr_t)D.msg & 1u) == 0) ? kMsgEven : 0u);
             tiles = (inf.n_bytes + tile_bytes - 1) / tile_bytes;
+            if (!(inf.bits & kVec) && len >= 2) {
+                // misaligned carrying bytes: message byte pairs from aligned
+                // vector pairs, in tiles of tile_bytes/16 pairs
+                const uint64_t tv = tile_bytes / 16u;
+                inf.per_tile = (uint32_t)tv;
+                ws.info[d] = inf;
+                ws.start[d] = 0ull;
+                ws.start_p[d] = 0ull;
+                ws.start_m[d] = ((len >> 1) + tv - 1) / tv;
+                stego_result r;
+                r.changed = 0;
+                r.sse = 0;
+                r.msg_bytes = len;
+                r.status = st;
+                r.reserved = 0;
+                results[d] = r;
+                continue;
+            }
         }
         ws.info[d] = inf;
         ws.start[d] = inf.mode ? 0ull : tiles;
         ws.start_p[d] = inf.mode ? tiles : 0ull;
+        ws.start_m[d] = 0ull;
         stego_result r;
         r.changed = 0;
         r.sse = 0;
@@ -371,11 +440,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles(WsView ws, uint32_t n
     __shared__ unsigned long long part[kScanThreads];
     const unsigned long long ts = scan_one(ws.start, n, part);
     const unsigned long long tp = scan_one(ws.start_p, n, part);
+    const unsigned long long tm = scan_one(ws.start_m, n, part);
     if (threadIdx.x == 0) {
         ws.head->total = ts;
         ws.head->counter = 0;
         ws.head->total_p = tp;
         ws.head->counter_p = 0;
+        ws.head->total_m = tm;
+        ws.head->counter_m = 0;
     }
 }
 
@@ -571,6 +643,107 @@ __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, 
     });
 }
 
+// One-bit stream covers whose buffers are not 16-byte aligned, in their own
+// tile space and kernels, so that the aligned kernels keep their register
+// budget (calling these routines from them raised persist_embed<4, true>
+// from 80 to 94 registers and persist_extract<4> from 39 to 64).  A tile is
+// per_tile aligned stego vectors (embed) or message byte pairs (extract);
+// the routines are the single-cover kernels' (same misalignment: vectors
+// after a scalar head; different misalignments: each stego vector joined
+// from the two aligned cover vectors around its bytes; extraction: each
+// message byte pair from the two aligned stego vectors around its bytes).
+template <int Q, bool STATS>
+__device__ __forceinline__ void mis_funnel(const s1::EmbedView &a, uint32_t h, uint32_t sel,
+                                           uint64_t j0, uint64_t j1, unsigned long long &changed,
+                                           unsigned long long &sse)
+{
+    s1::embed_funnel_range<Q, STATS>(a, h, sel, j0 + threadIdx.x, j1, blockDim.x, changed, sse);
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(512) persist_mis_embed(const stego_desc *descs, uint32_t n,
+                                                         stego_result *results, WsView ws)
+{
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
+    unsigned long long changed = 0, sse = 0;
+    uint32_t stat_d = 0xFFFFFFFFu;
+    claim_loop(ws.start_m, ws.head->total_m, &ws.head->counter_m, n,
+               [&](uint32_t d, unsigned long long lt) {
+        if (STATS && d != stat_d) {
+            flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+            stat_d = d;
+        }
+        const stego_desc &D = descs[d];
+        const DescInfo inf = ws.info[d];
+        s1::EmbedView a;
+        a.cover = D.cover;
+        a.stego = D.stego;
+        a.msg = D.msg;
+        a.n_bytes = inf.n_bytes;
+        a.t_bytes = inf.t_bytes;
+        a.slen = inf.len;
+        a.header = (inf.bits & kHeader) ? 1u : 0u;
+        a.nbits = inf.nbits;
+        a.msg_even = (inf.bits & kMsgEven) ? 1u : 0u;
+        a.pad = 0;
+        const uint32_t h = inf.W;
+        const uint64_t nvb = (inf.n_bytes - h) >> 4;
+        const uint64_t j0 = lt * inf.per_tile;
+        const uint64_t j1 = j0 + inf.per_tile < nvb ? j0 + inf.per_tile : nvb;
+        if (inf.bits & kFunnel) {
+            switch (inf.channels) {
+            case 0: mis_funnel<0, STATS>(a, h, inf.H, j0, j1, changed, sse); break;
+            case 1: mis_funnel<1, STATS>(a, h, inf.H, j0, j1, changed, sse); break;
+            case 2: mis_funnel<2, STATS>(a, h, inf.H, j0, j1, changed, sse); break;
+            default: mis_funnel<3, STATS>(a, h, inf.H, j0, j1, changed, sse); break;
+            }
+        } else {
+            s1::embed_shift_range<1, STATS>(a, h, j0 + threadIdx.x, j1, blockDim.x, changed,
+                                            sse);
+        }
+        // the h head bytes with the first tile, the tail (under one vector)
+        // with the last, one byte per thread
+        const uint32_t tail = (uint32_t)(inf.n_bytes - h - (nvb << 4));
+        uint64_t k = ~0ull;
+        if (lt == 0 && threadIdx.x < h)
+            k = threadIdx.x;
+        else if (j1 == nvb && threadIdx.x >= 16 && threadIdx.x - 16 < tail)
+            k = h + (nvb << 4) + (threadIdx.x - 16);
+        if (k != ~0ull) {
+            const uint32_t sb = k < a.t_bytes ? s1::stream_byte(a, k >> 3) : 0u;
+            s1::embed_one<STATS>(a, k, sb, changed, sse);
+        }
+    });
+    if (STATS)
+        flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+}
+
+__global__ void __launch_bounds__(512) persist_mis_extract(const stego_desc *descs, uint32_t n,
+                                                           WsView ws)
+{
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
+    claim_loop(ws.start_m, ws.head->total_m, &ws.head->counter_m, n,
+               [&](uint32_t d, unsigned long long lt) {
+        const stego_desc &D = descs[d];
+        const DescInfo inf = ws.info[d];
+        s1::ExtractView x;
+        x.st = D.cover;
+        x.msg = D.msg;
+        x.len = inf.len;
+        x.base = (inf.bits & kHeader) ? 32u : 0u;
+        x.msg_even = (inf.bits & kMsgEven) ? 1u : 0u;
+        x.pad = 0;
+        const uint64_t np = inf.len >> 1;
+        const uint64_t p0 = lt * inf.per_tile;
+        const uint64_t p1 = p0 + inf.per_tile < np ? p0 + inf.per_tile : np;
+        s1::extract_shift_range<1>(x, D.cover_bytes, p0 + threadIdx.x, p1, blockDim.x);
+        if (p1 == np && (x.len & 1u) && threadIdx.x == 0)
+            s1::extract_one(x, x.len - 1);
+    });
+}
+
 // The paper layout's own persistent kernels (a separate register budget from
 // the stream kernels): tiles of units, rows or runs, claimed like above.
 // Capped at 80 registers for three CTAs per SM: on 600 video frames the
@@ -682,6 +855,22 @@ int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint
     } else {
         void *args[] = {(void *)&d_descs, &n, &ws, (void *)&tile};
         e = launch_dependent(k, dim3(grid), dim3(sh.threads), args, 0, s);
+    }
+    if (e != cudaSuccess)
+        return STEGO_E_CUDA;
+    // misaligned stream tiles (count on the device; an empty set exits at once)
+    {
+        const void *km = EMBED ? (stats ? (const void *)persist_mis_embed<true>
+                                        : (const void *)persist_mis_embed<false>)
+                               : (const void *)persist_mis_extract;
+        const int gridm = persistent_grid(km, sh.threads, 0, sh.ctas_per_sm, ~0ull >> 1, 1);
+        if (EMBED) {
+            void *args[] = {(void *)&d_descs, &n, &d_results, &ws};
+            e = launch_dependent(km, dim3(gridm), dim3(sh.threads), args, 0, s);
+        } else {
+            void *args[] = {(void *)&d_descs, &n, &ws};
+            e = launch_dependent(km, dim3(gridm), dim3(sh.threads), args, 0, s);
+        }
     }
     if (e != cudaSuccess)
         return STEGO_E_CUDA;

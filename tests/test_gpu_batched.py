@@ -459,3 +459,81 @@ def test_kbit_descriptors_refused_per_cover(S, O):
     st, want = O.stream1_embed(covers[0], msgs[0], header=True)
     assert st == 0 and np.array_equal(sv[0].cpu().numpy(), want)
     assert bool((sv[1] == 0x5A).all()) and bool((sv[2] == 0x5A).all())
+
+
+def test_uneven_4096_misaligned_full_size(S, O):
+    """The 4096-cover uneven batch with every cover 1..15 bytes past a 16-byte
+    boundary: a third of the stegos at the cover's misalignment, a third at
+    another one, a third in place; messages at odd and even addresses.  The
+    misaligned tile space's kernels against the oracle on every cover (stego,
+    changed, sse) and every batched extraction from the misaligned stegos."""
+    items = synth.uneven_batch(4096)
+    rng = np.random.default_rng(4096)
+    n = len(items)
+    sizes = [it.cover_bytes for it in items]
+    mlens = [it.msg_bytes for it in items]
+    coff = [int(x) for x in rng.integers(1, 16, n)]
+    kind = [i % 3 for i in range(n)]  # 0 same misalignment, 1 another one, 2 in place
+    soff = [coff[i] if kind[i] != 1 else int((coff[i] + rng.integers(1, 15)) % 16)
+            for i in range(n)]
+    moff = [int(x) for x in rng.integers(0, 2, n)]
+    cpos, spos, mpos, p, q, r = [], [], [], 0, 0, 0
+    for i in range(n):
+        cpos.append(p + coff[i])
+        spos.append(q + soff[i])
+        mpos.append(r + moff[i])
+        p += (sizes[i] + 16 + 255) // 256 * 256
+        q += (sizes[i] + 16 + 255) // 256 * 256
+        r += (mlens[i] + 2 + 255) // 256 * 256
+    covers = synth.uniform_bytes(p, synth.substream(synth.SEED_BASE + 4, 1), "cuda")
+    orig = covers.clone()
+    stego = torch.full((q,), 0x5A, dtype=torch.uint8, device="cuda")
+    msgs = synth.uniform_bytes(r, synth.substream(synth.SEED_BASE + 4, 2), "cuda")
+    cv = [covers[cpos[i]:cpos[i] + sizes[i]] for i in range(n)]
+    sv = [cv[i] if kind[i] == 2 else stego[spos[i]:spos[i] + sizes[i]] for i in range(n)]
+    mv = [msgs[mpos[i]:mpos[i] + mlens[i]] for i in range(n)]
+    descs = S.descs_to_device(S.pack_descs(
+        [dict(cover=cv[i], stego=sv[i], msg=mv[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]))
+    res = S.new_result(n=n)
+    ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    S.stego_embed_batched(descs, n, res, S.FUSE_STATS, ws)
+    rr = S.read_result(res)
+    assert all(r_["status"] == 0 and r_["msg_bytes"] == mlens[i] for i, r_ in enumerate(rr))
+    out = torch.full((r,), 0xEE, dtype=torch.uint8, device="cuda")
+    ov = [out[mpos[i] + 1 - moff[i]:mpos[i] + 1 - moff[i] + mlens[i]] for i in range(n)]
+    descs_x = S.descs_to_device(S.pack_descs(
+        [dict(cover=sv[i], msg=ov[i], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in range(n)]))
+    res_x = S.new_result(n=n)
+    S.stego_extract_batched(descs_x, n, res_x, 0, ws)
+    rx = S.read_result(res_x)
+    assert all(r_["status"] == 0 and r_["msg_bytes"] == mlens[i] for i, r_ in enumerate(rx))
+    orig_h, cov_h, st_h = orig.cpu().numpy(), covers.cpu().numpy(), stego.cpu().numpy()
+    msg_h, out_h = msgs.cpu().numpy(), out.cpu().numpy()
+
+    def check(i):
+        c = orig_h[cpos[i]:cpos[i] + sizes[i]]
+        st, want = O.stream1_embed(c, msg_h[mpos[i]:mpos[i] + mlens[i]], header=True)
+        got = cov_h[cpos[i]:cpos[i] + sizes[i]] if kind[i] == 2 else \
+            st_h[spos[i]:spos[i] + sizes[i]]
+        if st != 0 or not np.array_equal(got, want):
+            return "embed"
+        if (rr[i]["changed"], rr[i]["sse"]) != O.changed_bytes(c, want):
+            return "stats"
+        if kind[i] != 2 and not np.array_equal(cov_h[cpos[i]:cpos[i] + sizes[i]], c):
+            return "cover written"
+        xs, xm = O.stream1_extract(want, cap=mlens[i], header=True)
+        o = mpos[i] + 1 - moff[i]
+        if xs != 0 or not np.array_equal(out_h[o:o + mlens[i]], xm):
+            return "extract"
+        return None
+
+    bad = [(i, e) for i, e in enumerate(pmap(check, n)) if e]
+    assert not bad, bad[:10]
+    # nothing outside the buffers was written
+    written = np.zeros(q, bool)
+    for i in range(n):
+        if kind[i] != 2:
+            written[spos[i]:spos[i] + sizes[i]] = True
+    assert np.all(st_h[~written] == 0x5A)
