@@ -650,14 +650,19 @@ __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, 
 // per_tile aligned stego vectors (embed) or message byte pairs (extract);
 // the routines are the single-cover kernels' (same misalignment: vectors
 // after a scalar head; different misalignments: each stego vector joined
-// from the two aligned cover vectors around its bytes; extraction: each
-// message byte pair from the two aligned stego vectors around its bytes).
+// from the two aligned cover vectors around its bytes; extraction: aligned
+// stego vectors reduced to their LSBs, a pair's bits cut from two lanes'),
+// two vectors per thread and round for the embeds, four for the
+// extraction.
+constexpr int kMisV = 2, kMisXV = 4;
+
 template <int Q, bool STATS>
 __device__ __forceinline__ void mis_funnel(const s1::EmbedView &a, uint32_t h, uint32_t sel,
                                            uint64_t j0, uint64_t j1, unsigned long long &changed,
                                            unsigned long long &sse)
 {
-    s1::embed_funnel_range<Q, STATS>(a, h, sel, j0 + threadIdx.x, j1, blockDim.x, changed, sse);
+    s1::embed_funnel_range<Q, STATS, kMisV>(a, h, sel, j0 + threadIdx.x, j1,
+                                            (uint64_t)blockDim.x * kMisV, changed, sse);
 }
 
 template <bool STATS>
@@ -699,8 +704,8 @@ __global__ void __launch_bounds__(512) persist_mis_embed(const stego_desc *descs
             default: mis_funnel<3, STATS>(a, h, inf.H, j0, j1, changed, sse); break;
             }
         } else {
-            s1::embed_shift_range<1, STATS>(a, h, j0 + threadIdx.x, j1, blockDim.x, changed,
-                                            sse);
+            s1::embed_shift_range<kMisV, STATS>(a, h, j0 + threadIdx.x, j1,
+                                                (uint64_t)blockDim.x * kMisV, changed, sse);
         }
         // the h head bytes with the first tile, the tail (under one vector)
         // with the last, one byte per thread
@@ -738,7 +743,8 @@ __global__ void __launch_bounds__(512) persist_mis_extract(const stego_desc *des
         const uint64_t np = inf.len >> 1;
         const uint64_t p0 = lt * inf.per_tile;
         const uint64_t p1 = p0 + inf.per_tile < np ? p0 + inf.per_tile : np;
-        s1::extract_shift_range<1>(x, D.cover_bytes, p0 + threadIdx.x, p1, blockDim.x);
+        s1::extract_shift_lsb<kMisXV>(x, D.cover_bytes, p0, p1, threadIdx.x >> 5,
+                                      blockDim.x >> 5);
         if (p1 == np && (x.len & 1u) && threadIdx.x == 0)
             s1::extract_one(x, x.len - 1);
     });

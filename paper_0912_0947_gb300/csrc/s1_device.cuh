@@ -200,13 +200,61 @@ __device__ __forceinline__ uint32_t stream_byte_or0(const EmbedView &a, uint64_t
 
 // The stream bits of cover bytes k0..k0+15 for any k0, as S[2v] | S[2v+1]
 // << 8 would give them for k0 = 16v: three stream bytes, cut at bit k0 % 8.
+// Inside the message (stream bytes q-3 .. q+7 all message bytes) the three
+// come from the two aligned 32-bit words around them, joined by a funnel
+// shift; elsewhere byte by byte.
 __device__ __forceinline__ uint32_t stream_bits16(const EmbedView &a, uint64_t k0)
 {
     const uint64_t q = k0 >> 3;
-    const uint32_t w = (stream_byte_or0(a, q) << 16) | (stream_byte_or0(a, q + 1) << 8) |
-                       stream_byte_or0(a, q + 2);
+    const uint64_t hdr = a.header ? 4u : 0u;
+    uint32_t w;
+    if (q >= hdr + 3 && q + 7 < a.slen) {
+        const uintptr_t pa = (uintptr_t)(a.msg + (q - hdr));
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(pa & ~(uintptr_t)3u);
+        const uint32_t b = __funnelshift_r(__ldg(wp), __ldg(wp + 1), 8u * (uint32_t)(pa & 3u));
+        w = __byte_perm(b, 0u, 0x4012u); // S[q] << 16 | S[q+1] << 8 | S[q+2]
+    } else {
+        w = (stream_byte_or0(a, q) << 16) | (stream_byte_or0(a, q + 1) << 8) |
+            stream_byte_or0(a, q + 2);
+    }
     const uint32_t bits = (w >> (8u - (uint32_t)(k0 & 7u))) & 0xFFFFu; // byte k0's bit on top
     return (bits >> 8) | ((bits & 0xFFu) << 8);
+}
+
+// stream_bits16 where stream bytes q-3 .. q+7 (q = k0 / 8) are known to be
+// message bytes: no test.
+__device__ __forceinline__ uint32_t stream_bits16_inner(const EmbedView &a, uint64_t k0)
+{
+    const uint64_t q = k0 >> 3;
+    const uintptr_t pa = (uintptr_t)(a.msg + (q - (a.header ? 4u : 0u)));
+    const uint32_t *wp = reinterpret_cast<const uint32_t *>(pa & ~(uintptr_t)3u);
+    const uint32_t b = __funnelshift_r(__ldg(wp), __ldg(wp + 1), 8u * (uint32_t)(pa & 3u));
+    const uint32_t w = __byte_perm(b, 0u, 0x4012u);
+    const uint32_t bits = (w >> (8u - (uint32_t)(k0 & 7u))) & 0xFFFFu;
+    return (bits >> 8) | ((bits & 0xFFu) << 8);
+}
+
+// Cover vector c with its 16 stream bits p (as S[2v] | S[2v+1] << 8) ->
+// stego vector, all 16 bytes carrying.
+__device__ __forceinline__ uint4 spread16(const uint4 &c, uint32_t p)
+{
+    const uint32_t r0 = __byte_perm(p, 0u, 0x0000u);
+    const uint32_t r1 = __byte_perm(p, 0u, 0x1111u);
+    uint4 o;
+    o.x = (c.x & 0xFEFEFEFEu) | spread_hi(r0);
+    o.y = (c.y & 0xFEFEFEFEu) | spread_lo(r0);
+    o.z = (c.z & 0xFEFEFEFEu) | spread_hi(r1);
+    o.w = (c.w & 0xFEFEFEFEu) | spread_lo(r1);
+    return o;
+}
+
+// Whether the vectors at cover bytes k_first .. k_last + 15 (k = h + 16j)
+// all carry stream bits in every byte and have their stream windows inside
+// the message (the fast paths' condition).
+__device__ __forceinline__ bool window_inner(const EmbedView &a, uint64_t k_first, uint64_t k_last)
+{
+    const uint64_t hdr = a.header ? 4u : 0u;
+    return k_last + 16u <= a.t_bytes && (k_first >> 3) >= hdr + 3u && (k_last >> 3) + 7u < a.slen;
 }
 
 // A vector that holds the end of the carrying bytes: bytes from t on keep
@@ -262,23 +310,33 @@ __device__ __forceinline__ void embed_shift_range(const EmbedView &a, uint32_t h
     for (uint64_t j0 = j_first; j0 < j_end; j0 += step) {
         uint4 c[V];
         uint32_t p[V];
+        const uint64_t jl = j0 + (uint64_t)(V - 1) * blockDim.x;
+        if (jl < j_end && window_inner(a, h + (j0 << 4), h + (jl << 4))) {
+            // the whole round inside the message: no per-vector checks
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t j = j0 + (uint64_t)u * blockDim.x;
-            if (j < j_end)
-                c[u] = __ldcs(src + j);
+            for (int u = 0; u < V; ++u)
+                c[u] = __ldcs(src + j0 + (uint64_t)u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                p[u] = stream_bits16_inner(a, h + ((j0 + (uint64_t)u * blockDim.x) << 4));
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                const uint4 o = spread16(c[u], p[u]);
+                if (STATS)
+                    n += vec_changes(o, c[u]);
+                __stcs(dst + j0 + (uint64_t)u * blockDim.x, o);
+            }
+            continue;
         }
-#pragma unroll
+        // a round at an edge: one vector at a time, with the checks
+#pragma unroll 1
         for (int u = 0; u < V; ++u) {
             const uint64_t j = j0 + (uint64_t)u * blockDim.x;
+            if (j >= j_end)
+                break;
             const uint64_t k0 = h + (j << 4);
-            p[u] = (j < j_end && k0 < a.t_bytes) ? stream_bits16(a, k0) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t j = j0 + (uint64_t)u * blockDim.x;
-            if (j < j_end)
-                __stcs(dst + j, embed_vec16_at<STATS>(a, h + (j << 4), c[u], p[u], n));
+            const uint32_t pw = k0 < a.t_bytes ? stream_bits16(a, k0) : 0u;
+            __stcs(dst + j, embed_vec16_at<STATS>(a, k0, __ldcs(src + j), pw, n));
         }
     }
     if (STATS) {
@@ -305,7 +363,7 @@ __device__ __forceinline__ uint4 funnel16(const uint4 &lo, const uint4 &hi, uint
 // each loaded whole, joined by funnel16.  A vector whose two cover vectors
 // are not both inside the cover reads its 16 cover bytes one by one.  Head
 // and tail bytes are left to the caller.
-template <int Q, bool STATS>
+template <int Q, bool STATS, int V = 1>
 __device__ __forceinline__ void embed_funnel_range(const EmbedView &a, uint32_t h, uint32_t sel,
                                                    uint64_t j_first, uint64_t j_end,
                                                    uint64_t step, unsigned long long &changed,
@@ -316,7 +374,41 @@ __device__ __forceinline__ void embed_funnel_range(const EmbedView &a, uint32_t 
     const uintptr_t lo_ok = (uintptr_t)a.cover, hi_ok = (uintptr_t)a.cover + a.n_bytes;
     uint4 *dst = reinterpret_cast<uint4 *>(a.stego + h);
     uint32_t n = 0;
-    for (uint64_t j = j_first; j < j_end; j += step) {
+    // stego vectors [safe_lo, safe_hi) have both cover vectors inside the cover
+    const uint64_t safe_lo = (uintptr_t)A >= lo_ok ? 0u : 1u;
+    const uint64_t nv = (hi_ok - (uintptr_t)A) >> 4;
+    const uint64_t safe_hi = nv >= 1 ? nv - 1 : 0u;
+    const uint64_t vstep = V > 1 ? step / V : step; // the V vectors of a round
+    for (uint64_t j0 = j_first; j0 < j_end; j0 += step) {
+        const uint64_t jl = j0 + (uint64_t)(V - 1) * vstep;
+        if (jl < j_end && j0 >= safe_lo && jl < safe_hi &&
+            window_inner(a, h + (j0 << 4), h + (jl << 4))) {
+            // the whole round inside: no per-vector checks
+            uint4 lo[V], hi[V];
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                lo[u] = __ldcs(A + j0 + (uint64_t)u * vstep);
+                hi[u] = __ldcs(A + j0 + (uint64_t)u * vstep + 1);
+            }
+            uint32_t p[V];
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                p[u] = stream_bits16_inner(a, h + ((j0 + (uint64_t)u * vstep) << 4));
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                const uint4 c = funnel16<Q>(lo[u], hi[u], sel);
+                const uint4 o = spread16(c, p[u]);
+                if (STATS)
+                    n += vec_changes(o, c);
+                __stcs(dst + j0 + (uint64_t)u * vstep, o);
+            }
+            continue;
+        }
+#pragma unroll 1
+        for (int u = 0; u < V; ++u) {
+        const uint64_t j = j0 + (uint64_t)u * vstep;
+        if (j >= j_end)
+            break;
         const uintptr_t b = (uintptr_t)(A + j);
         const uint64_t k0 = h + (j << 4);
         uint4 c;
@@ -332,6 +424,7 @@ __device__ __forceinline__ void embed_funnel_range(const EmbedView &a, uint32_t 
         }
         const uint32_t p = k0 < a.t_bytes ? stream_bits16(a, k0) : 0u;
         __stcs(dst + j, embed_vec16_at<STATS>(a, k0, c, p, n));
+        }
     }
     if (STATS) {
         changed += n;
@@ -466,51 +559,92 @@ __device__ __forceinline__ void extract_bytes_range(const ExtractView &x, uint64
         extract_one(x, q);
 }
 
-// The LSBs of 32 bytes (two vectors) as one word, first byte on top.
-__device__ __forceinline__ uint32_t lsb32(const uint4 &lo, const uint4 &hi)
+// The 16 LSBs of an aligned stego vector, its first byte's on top.
+__device__ __forceinline__ uint32_t lsb16(const uint4 &c)
 {
-    return (gather4(lo.x) << 28) | (gather4(lo.y) << 24) | (gather4(lo.z) << 20) |
-           (gather4(lo.w) << 16) | (gather4(hi.x) << 12) | (gather4(hi.y) << 8) |
-           (gather4(hi.z) << 4) | gather4(hi.w);
+    return (gather4(c.x) << 12) | (gather4(c.y) << 8) | (gather4(c.z) << 4) | gather4(c.w);
 }
 
-// A stego whose carrying bytes (st + base) are not 16-byte aligned (a =
-// their address mod 16): message bytes 2v, 2v+1 come from the two aligned
-// vectors around stego bytes base + 16v .. base + 16v + 15, cut at a.  A
-// pair whose two vectors are not both inside the stego goes byte by byte.
+// A misaligned stego (a = its carrying bytes' address mod 16), warp by warp:
+// lane l of a round loads aligned vector r + 32u + l once and reduces it to
+// its 16 LSBs; the pair starting a bytes into vector v takes the low 16 - a
+// of them and the top a LSBs of vector v + 1, which come from the next lane
+// by one shuffle (from lane 0 of the next unit, or a load of the last lane,
+// at the end of a unit).  Pairs v in [v_lo, v_hi); warp `warp` of `nwarps`
+// takes rounds of 32*V pairs.  Pairs whose two vectors are not both inside
+// the stego go byte by byte.
 template <int V>
-__device__ __forceinline__ void extract_shift_range(const ExtractView &x, uint64_t C,
-                                                    uint64_t v_first, uint64_t v_end,
-                                                    uint64_t step)
+__device__ __forceinline__ void extract_shift_lsb(const ExtractView &x, uint64_t C, uint64_t v_lo,
+                                                  uint64_t v_hi, uint64_t warp, uint64_t nwarps)
 {
     const uintptr_t p0 = (uintptr_t)(x.st + x.base);
     const uint32_t a = (uint32_t)(p0 & 15u);
     const uint4 *__restrict__ A = reinterpret_cast<const uint4 *>(p0 - a);
     const uintptr_t lo_ok = (uintptr_t)x.st, hi_ok = (uintptr_t)x.st + C;
-    for (uint64_t v0 = v_first; v0 < v_end; v0 += step) {
-        uint4 lo[V], hi[V];
-        bool fast[V];
+    const uint32_t lane = threadIdx.x & 31u;
+    // pairs [safe_lo, safe_hi) have both vectors inside the stego
+    const uint64_t safe_lo = (uintptr_t)A >= lo_ok ? 0u : 1u;
+    const uint64_t nv = (hi_ok - (uintptr_t)A) >> 4; // vectors of A inside the stego
+    const uint64_t safe_hi = nv >= 1 ? (nv - 1 < v_hi ? nv - 1 : v_hi) : 0u;
+    for (uint64_t r = v_lo + warp * 32u * V; r < v_hi; r += nwarps * 32u * V) {
+        if (r >= safe_lo && r + 32u * V <= safe_hi) {
+            // the whole round inside: no per-pair checks
+            uint4 c[V];
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
-            const uintptr_t b = (uintptr_t)(A + v);
-            fast[u] = v < v_end && b >= lo_ok && b + 32u <= hi_ok;
-            if (fast[u]) {
-                lo[u] = __ldcs(A + v);
-                hi[u] = __ldcs(A + v + 1);
+            for (int u = 0; u < V; ++u)
+                c[u] = __ldcs(A + r + (uint64_t)u * 32u + lane);
+            uint4 e = make_uint4(0u, 0u, 0u, 0u);
+            if (lane == 31u)
+                e = __ldcs(A + r + (uint64_t)V * 32u);
+            uint32_t L[V];
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                L[u] = lsb16(c[u]);
+            const uint32_t Le = lsb16(e);
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, L[u], 1);
+                const uint32_t first =
+                    u + 1 < V ? __shfl_sync(0xFFFFFFFFu, L[u + 1 < V ? u + 1 : u], 0) : Le;
+                if (lane == 31u)
+                    nx = first;
+                const uint32_t bits = ((L[u] << a) | (nx >> (16u - a))) & 0xFFFFu;
+                const uint32_t pair = (bits >> 8) | ((bits & 0xFFu) << 8);
+                const uint64_t v = r + (uint64_t)u * 32u + lane;
+                if (x.msg_even) {
+                    *reinterpret_cast<unsigned short *>(x.msg + 2 * v) = (unsigned short)pair;
+                } else {
+                    x.msg[2 * v] = (uint8_t)pair;
+                    x.msg[2 * v + 1] = (uint8_t)(pair >> 8);
+                }
             }
+            continue;
         }
-#pragma unroll
+        // a round at an edge: one unit at a time, with the checks
+#pragma unroll 1
         for (int u = 0; u < V; ++u) {
-            const uint64_t v = v0 + (uint64_t)u * blockDim.x;
-            if (v >= v_end)
+            const uint64_t v = r + (uint64_t)u * 32u + lane;
+            const uintptr_t b = (uintptr_t)(A + v);
+            uint4 c = make_uint4(0u, 0u, 0u, 0u);
+            if (v <= v_hi && b >= lo_ok && b + 16u <= hi_ok)
+                c = __ldcs(A + v);
+            const uint64_t ve = r + (uint64_t)u * 32u + 32u;
+            const uintptr_t be = (uintptr_t)(A + ve);
+            uint4 e = make_uint4(0u, 0u, 0u, 0u);
+            if (lane == 31u && ve <= v_hi && be >= lo_ok && be + 16u <= hi_ok)
+                e = __ldcs(A + ve);
+            const uint32_t L = lsb16(c);
+            uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, L, 1);
+            if (lane == 31u)
+                nx = lsb16(e);
+            if (v >= v_hi)
                 continue;
-            if (!fast[u]) {
+            if (!(b >= lo_ok && b + 32u <= hi_ok)) {
                 extract_one(x, 2 * v);
                 extract_one(x, 2 * v + 1);
                 continue;
             }
-            const uint32_t bits = (lsb32(lo[u], hi[u]) >> (16u - a)) & 0xFFFFu;
+            const uint32_t bits = ((L << a) | (nx >> (16u - a))) & 0xFFFFu;
             const uint32_t pair = (bits >> 8) | ((bits & 0xFFu) << 8);
             if (x.msg_even) {
                 *reinterpret_cast<unsigned short *>(x.msg + 2 * v) = (unsigned short)pair;

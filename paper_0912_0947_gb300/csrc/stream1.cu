@@ -11,8 +11,11 @@
 // vectors in flight per thread over a persistent grid feed HBM directly.
 // Misaligned buffers: cover and stego with the same address mod 16 run
 // aligned vectors after a head of scalar bytes (the stream cut at the head's
-// bit offset); a misaligned stego is read as aligned vector pairs; only an
-// embed whose cover and stego differ mod 16 runs byte by byte.
+// bit offset); cover and stego at different addresses mod 16 build each
+// aligned stego vector from the two aligned cover vectors around its bytes;
+// a misaligned stego is read as aligned vectors, each reduced to its 16
+// LSBs, a pair's second part coming from the next lane.  Rounds wholly
+// inside the buffers and the message run without per-vector checks.
 #include "s1_device.cuh"
 
 namespace stego {
@@ -103,9 +106,10 @@ __global__ void __launch_bounds__(512) embed_shift(EmbedArgs e, uint32_t h)
 
 // Cover and stego at different addresses mod 16, out of place: aligned
 // stego vectors after h head bytes, each from two aligned cover vectors
-// (cover + h is 4Q + b bytes past a 16-byte boundary); block 0 does the head
-// and the tail (fewer than 32 bytes).  Requires n_bytes >= h.
-template <int Q, bool STATS>
+// (cover + h is 4Q + b bytes past a 16-byte boundary), V of them per thread
+// and round; block 0 does the head and the tail (fewer than 32 bytes).
+// Requires n_bytes >= h.
+template <int Q, int V, bool STATS>
 __global__ void __launch_bounds__(512) embed_funnel(EmbedArgs e, uint32_t h, uint32_t sel)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
@@ -113,8 +117,9 @@ __global__ void __launch_bounds__(512) embed_funnel(EmbedArgs e, uint32_t h, uin
     unsigned long long changed = 0, sse = 0;
     write_res(e, STATS);
     const uint64_t nvb = (e.a.n_bytes - h) >> 4;
-    s1::embed_funnel_range<Q, STATS>(e.a, h, sel, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                     nvb, (uint64_t)gridDim.x * blockDim.x, changed, sse);
+    s1::embed_funnel_range<Q, STATS, V>(e.a, h, sel,
+                                        (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nvb,
+                                        (uint64_t)gridDim.x * blockDim.x * V, changed, sse);
     if (blockIdx.x == 0)
         head_tail<STATS>(e.a, h, nvb, changed, sse);
     if (STATS)
@@ -187,8 +192,10 @@ __global__ void __launch_bounds__(512) extract_vec(ExtractArgs a)
         s1::extract_one(x, x.len - 1);
 }
 
-// A stego that is not 16-byte aligned: each message byte pair from the two
-// aligned vectors around its 16 stego bytes.
+// A stego that is not 16-byte aligned: the warps of the grid take rounds
+// of 32*V message byte pairs; each aligned stego vector is loaded once and
+// reduced to its 16 LSBs, a pair's bits cut from its own and the next
+// lane's.
 template <int V>
 __global__ void __launch_bounds__(512) extract_shift(ExtractArgs a)
 {
@@ -197,19 +204,25 @@ __global__ void __launch_bounds__(512) extract_shift(ExtractArgs a)
     ExtractView x;
     if (extract_prologue(a, x) != STEGO_OK)
         return;
-    s1::extract_shift_range<V>(x, a.C, (uint64_t)blockIdx.x * blockDim.x * V + threadIdx.x,
-                               x.len >> 1, (uint64_t)gridDim.x * blockDim.x * V);
+    const uint64_t wpb = blockDim.x >> 5;
+    s1::extract_shift_lsb<V>(x, a.C, 0, x.len >> 1,
+                             (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5),
+                             (uint64_t)gridDim.x * wpb);
     if ((x.len & 1u) && blockIdx.x == 0 && threadIdx.x == 0)
         s1::extract_one(x, x.len - 1);
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Vectors in flight per thread in the misaligned kernels (their stream
-// windows and vector pairs take more registers than the aligned ones; on the
-// 201 MB cover two ran slower than one: embed 95.8 against 88.1 us, extract
-// 50.8 against 49.2 us).
-constexpr int kShiftV = 1;
+// Vectors in flight per thread in the misaligned kernels, measured on the
+// 201 MB cover at full capacity (with the check-free interior rounds):
+// same misalignment embed 69.6 / 69.7 / 69.2 us for 1 / 2 / 4 (83-88 us
+// before those rounds); different misalignments 82.7 / 72.4-73.7 / 71.7-84.7
+// us; extraction 48.7 (vector pairs, one per thread) / 43-44 / 36.1-36.9 us
+// (LSB words shuffled between lanes).
+constexpr int kShiftV = 2;
+constexpr int kFunnelV = 2;
+constexpr int kExtractShiftV = 4;
 
 int clamp_vec(int v) { return (v == 1 || v == 2 || v == 8) ? v : 4; }
 
@@ -267,14 +280,15 @@ cudaError_t s1_embed(const uint8_t *cover, uint8_t *stego, uint64_t n_bytes, uin
         const uint32_t d = (uint32_t)(((uintptr_t)cover + hs) & 15u), b = d & 3u;
         const uint32_t sel = b | ((b + 1) << 4) | ((b + 2) << 8) | ((b + 3) << 12);
         const void *k;
+        constexpr int F = kFunnelV;
         switch (d >> 2) {
-        case 0: k = stats ? (const void *)embed_funnel<0, true> : (const void *)embed_funnel<0, false>; break;
-        case 1: k = stats ? (const void *)embed_funnel<1, true> : (const void *)embed_funnel<1, false>; break;
-        case 2: k = stats ? (const void *)embed_funnel<2, true> : (const void *)embed_funnel<2, false>; break;
-        default: k = stats ? (const void *)embed_funnel<3, true> : (const void *)embed_funnel<3, false>; break;
+        case 0: k = stats ? (const void *)embed_funnel<0, F, true> : (const void *)embed_funnel<0, F, false>; break;
+        case 1: k = stats ? (const void *)embed_funnel<1, F, true> : (const void *)embed_funnel<1, F, false>; break;
+        case 2: k = stats ? (const void *)embed_funnel<2, F, true> : (const void *)embed_funnel<2, F, false>; break;
+        default: k = stats ? (const void *)embed_funnel<3, F, true> : (const void *)embed_funnel<3, F, false>; break;
         }
         const uint64_t nvb = (n_bytes - hs) >> 4;
-        const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvb, (uint64_t)T);
+        const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, nvb, (uint64_t)T * F);
         void *fargs[] = {&e, (void *)&hs, (void *)&sel};
         return launch_dependent(k, dim3(grid), dim3(T), fargs, 0, s);
     }
@@ -322,10 +336,10 @@ cudaError_t s1_extract(const uint8_t *st, uint64_t C, uint8_t *msg, uint64_t cap
                                          (uint64_t)T * vec);
         return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
     }
-    const void *k = (const void *)extract_shift<kShiftV>;
+    const void *k = (const void *)extract_shift<kExtractShiftV>;
     const uint64_t npairs = max_len >> 1;
     const int grid = persistent_grid(k, T, 0, sh.ctas_per_sm, npairs > 0 ? npairs : 1,
-                                     (uint64_t)T * kShiftV);
+                                     (uint64_t)T * kExtractShiftV);
     return launch_dependent(k, dim3(grid), dim3(T), args, 0, s);
 }
 
