@@ -685,11 +685,16 @@ def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None):
             "outputs_identical_to_aligned": same}
 
 
-def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds=1.0):
+def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=1000000, seconds=20.0,
+                    saturation_rates=(100000, 200000, 500000, 1000000, 2000000, 3000000,
+                                      5000000)):
     """Open-loop Poisson request stream against the continuous-batching
     server: 70% embed / 30% extract over a resident pool of 4096 uneven covers
     (sizes as in the batched leg) and their pre-embedded stegos, messages and
-    outputs resident on the device, 40 GB in-flight budget."""
+    outputs resident on the device, 40 GB in-flight budget.  Each offered
+    rate runs `seconds` of arrivals (at most max_requests); after the listed
+    rates the offered rate keeps rising until the server no longer keeps up
+    (throughput under 90% of the offered rate): the knee."""
     import numpy as np
     items = synth.uneven_batch(4096)
     sizes = [it.cover_bytes for it in items]
@@ -715,19 +720,21 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds
     torch.cuda.synchronize()
     base = {"cover": covers.data_ptr(), "stego": stegos.data_ptr(), "out_st": out_st.data_ptr(),
             "msg": msgs.data_ptr(), "out_msg": out_msg.data_ptr()}
+    off_a = np.array(off, dtype=np.uint64)
+    moff_a = np.array(moff, dtype=np.uint64)
+    size_a = np.array(sizes, dtype=np.uint64)
+    mlen_a = np.array(mlens, dtype=np.uint64)
     results = []
     embedded, extracted = set(), set()
-    srv = S.Server(slots=8, max_batch=512, budget_bytes=40 << 30, device=dev)
-    for ri, rate in enumerate(rates):
+    total_batches = 0
+
+    def one_rate(ri, rate):
         cnt = int(min(max_requests, max(500, rate * seconds)))
         u = synth.uniform_floats_np(2 * cnt, synth.substream(synth.SEED_BASE + 5, 100 + ri))
         ids = np.minimum((u[:cnt] * n).astype(np.int64), n - 1)
         is_ext = u[cnt:] < 0.3
         reqs = np.zeros(cnt, dtype=S.REQUEST_DTYPE)
-        o = np.array(off, dtype=np.uint64)[ids]
-        mo = np.array(moff, dtype=np.uint64)[ids]
-        cb = np.array(sizes, dtype=np.uint64)[ids]
-        mb = np.array(mlens, dtype=np.uint64)[ids]
+        o, mo, cb, mb = off_a[ids], moff_a[ids], size_a[ids], mlen_a[ids]
         reqs["op"] = np.where(is_ext, S.OP_EXTRACT, S.OP_EMBED)
         reqs["flags"] = S.HEADER_BE32
         reqs["cover"] = np.where(is_ext, base["stego"] + o, base["cover"] + o)
@@ -735,26 +742,39 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds
         reqs["msg"] = np.where(is_ext, base["out_msg"] + mo, base["msg"] + mo)
         reqs["cover_bytes"] = cb
         reqs["msg_bytes"] = mb
-        arr = synth.poisson_arrivals(float(rate), cnt, synth.substream(synth.SEED_BASE + 5, 200 + ri))
-        comps = srv.run_open_loop(reqs, arr, timeout_s=120)
+        arr = synth.poisson_arrivals(float(rate), cnt,
+                                     synth.substream(synth.SEED_BASE + 5, 200 + ri))
+        srv = S.Server(slots=8, max_batch=512, budget_bytes=40 << 30, device=dev)
+        comps = srv.run_open_loop(reqs, arr, timeout_s=600)
+        stats = srv.stats()
+        srv.close()
         embedded.update(int(i) for i in ids[~is_ext][:64])
         extracted.update(int(i) for i in ids[is_ext][:64])
-        st = comps["status"]
-        assert np.all(st == 0), "serving requests failed"
+        assert np.all(comps["status"] == 0), "serving requests failed"
         lat = (comps["t_done"] - comps["t_submit"]) * 1e3
         span = float(comps["t_done"].max() - comps["t_submit"].min())
-        bytes_ = float(cb.sum())
-        results.append({
+        return {
             "offered_req_per_s": rate, "requests": cnt,
+            "arrival_span_s": round(float(arr[-1]), 3),
             "throughput_req_per_s": round(cnt / span, 1),
-            "cover_gbs": round(bytes_ / span / 1e9, 2),
+            "cover_gbs": round(float(cb.sum()) / span / 1e9, 2),
             "p50_ms": round(float(np.percentile(lat, 50)), 4),
             "p99_ms": round(float(np.percentile(lat, 99)), 4),
             "max_ms": round(float(lat.max()), 4),
             "mean_batch": round(float(comps["batch_size"].mean()), 2),
-        })
-    stats = srv.stats()
-    srv.close()
+            "batches": stats["batches"],
+            "peak_in_flight_bytes": stats["peak_in_flight_bytes"],
+        }
+
+    for ri, rate in enumerate(rates):
+        results.append(one_rate(ri, rate))
+    knee = None
+    for k, rate in enumerate(saturation_rates):
+        r = one_rate(len(rates) + k, rate)
+        results.append(r)
+        if r["throughput_req_per_s"] < 0.9 * rate:
+            knee = r
+            break
     # served outputs equal single calls (a sample of the covers embedded)
     for i in sorted(embedded)[:64]:
         ref = torch.empty(sizes[i], dtype=torch.uint8, device=dev)
@@ -763,11 +783,14 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=20000, seconds
         assert torch.equal(ref, out_st[off[i]:off[i] + sizes[i]])
     for i in sorted(extracted)[:64]:
         assert torch.equal(out_msg[moff[i]:moff[i] + mlens[i]], msgs[moff[i]:moff[i] + mlens[i]])
+    kept = [r for r in results if r["throughput_req_per_s"] >= 0.9 * r["offered_req_per_s"]]
     return {"workload": "Poisson open loop, 70% embed / 30% extract, 4096 resident uneven "
                         "covers and stegos, 40 GB in-flight budget, 8 slots, batches <= 512",
-            "per_rate": "max(500, min(%d, rate x %g s)) requests" % (max_requests, seconds),
-            "rates": results, "batches": stats["batches"],
-            "peak_in_flight_bytes": stats["peak_in_flight_bytes"]}
+            "per_rate": "max(500, min(%d, rate x %g s)) requests, a new server per rate" % (
+                max_requests, seconds),
+            "rates": results,
+            "max_sustained": kept[-1] if kept else None,
+            "knee": knee if knee else {"note": "no saturation up to %d req/s" % saturation_rates[-1]}}
 
 
 def run_paper2_leg(S, AT, torch, dev, synth):
@@ -1410,9 +1433,9 @@ def main():
                     help="fixed launch shape threads,vec,ctas_per_sm,tile_bytes for the embed "
                          "(tile_bytes > 0: shared-memory staged kernel with that ring)")
     ap.add_argument("--shape-extract", default="", help="same for the extract")
-    ap.add_argument("--serving-seconds", type=float, default=1.0,
-                    help="arrival span per rate of the serving leg (20 for 20 s per rate)")
-    ap.add_argument("--serving-max-requests", type=int, default=20000,
+    ap.add_argument("--serving-seconds", type=float, default=20.0,
+                    help="arrival span per rate of the serving leg")
+    ap.add_argument("--serving-max-requests", type=int, default=1000000,
                     help="request cap per rate of the serving leg")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

@@ -366,9 +366,10 @@ typedef struct stego_server_config {
 
 typedef struct stego_request {
     uint32_t op;           /* STEGO_OP_EMBED or STEGO_OP_EXTRACT            */
-    uint32_t flags;        /* STEGO_LAYOUT_STREAM1 [| STEGO_HEADER_BE32];   */
-                           /* other layouts and bits per byte complete with */
-                           /* STEGO_E_INVAL (a request has no geometry)     */
+    uint32_t flags;        /* as stego_desc.flags: STEGO_LAYOUT_STREAM1     */
+                           /* [| STEGO_HEADER_BE32] or STEGO_LAYOUT_PAPER2  */
+                           /* (with geom); k-bit and one-plane stream       */
+                           /* requests complete with STEGO_E_INVAL          */
     const uint8_t *cover;  /* embed: cover; extract: stego image            */
     uint8_t *stego;        /* embed: output image                           */
     uint8_t *msg;          /* embed: message (read); extract: output buffer */
@@ -376,7 +377,8 @@ typedef struct stego_request {
     uint64_t msg_bytes;    /* embed: length; extract: capacity of msg       */
     uint64_t msg_len;      /* extract without a header: bytes to extract    */
     uint64_t tag;          /* returned in the completion                    */
-} stego_request;           /* 64 bytes */
+    stego_geom geom;       /* STEGO_LAYOUT_PAPER2 geometry                  */
+} stego_request;           /* 80 bytes */
 
 typedef struct stego_completion {
     uint64_t tag;

@@ -97,17 +97,18 @@ HOST_JOB_DTYPE = np.dtype([
 ])
 assert HOST_JOB_DTYPE.itemsize == 80
 
-# stego_request / stego_completion as laid out in host memory (64 bytes each)
+# stego_request (80 bytes) / stego_completion (64 bytes) as laid out in host memory
 REQUEST_DTYPE = np.dtype([
     ("op", "<u4"), ("flags", "<u4"), ("cover", "<u8"), ("stego", "<u8"), ("msg", "<u8"),
     ("cover_bytes", "<u8"), ("msg_bytes", "<u8"), ("msg_len", "<u8"), ("tag", "<u8"),
+    ("width", "<u4"), ("height", "<u4"), ("channels", "<u4"), ("plane", "<u4"),
 ])
 COMPLETION_DTYPE = np.dtype([
     ("tag", "<u8"), ("changed", "<u8"), ("sse", "<u8"), ("msg_bytes", "<u8"),
     ("status", "<i4"), ("batch_size", "<i4"),
     ("t_submit", "<f8"), ("t_dispatch", "<f8"), ("t_done", "<f8"),
 ])
-assert REQUEST_DTYPE.itemsize == 64 and COMPLETION_DTYPE.itemsize == 64
+assert REQUEST_DTYPE.itemsize == 80 and COMPLETION_DTYPE.itemsize == 64
 
 _LIB = None
 _vp = ctypes.c_void_p

@@ -608,6 +608,6 @@ static_assert(sizeof(stego_result) == 32, "stego_result layout");
 static_assert(sizeof(stego_geom) == 16, "stego_geom layout");
 static_assert(sizeof(stego_tune) == 16, "stego_tune layout");
 static_assert(sizeof(stego::StatSlot) == 32, "statistics slot layout");
-static_assert(sizeof(stego_request) == 64, "stego_request layout");
+static_assert(sizeof(stego_request) == 80, "stego_request layout");
 static_assert(sizeof(stego_completion) == 64, "stego_completion layout");
 static_assert(sizeof(stego_server_config) == 48, "stego_server_config layout");

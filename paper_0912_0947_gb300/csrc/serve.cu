@@ -220,6 +220,7 @@ struct stego_server {
                 d.msg_bytes = m.p.req.msg_bytes;
                 d.msg_len = m.p.req.msg_len;
                 d.flags = m.p.req.flags;
+                d.geom = m.p.req.geom;
                 (m.embed ? s.h_desc_e : s.h_desc_x)[m.index] = d;
             }
             int st = STEGO_OK;

@@ -85,7 +85,7 @@ def test_alone_equals_mix(S):
     # mix: open-loop Poisson arrivals, four slots, batches of up to 64
     pool.reset_outputs()
     srv = S.Server(slots=4, max_batch=64, budget_bytes=1 << 34)
-    arrivals = synth.poisson_arrivals(50000.0, n_req, 77)
+    arrivals = synth.poisson_arrivals(200000.0, n_req, 77)
     comps = srv.run_open_loop(pool.reqs, arrivals, timeout_s=60)
     st = srv.stats()
     srv.close()
@@ -98,9 +98,19 @@ def test_alone_equals_mix(S):
     m_out = pool.snapshot()
     for r in range(n_req):
         assert torch.equal(m_out[r], a_out[r]), r
-    # the mix really batched and overlapped
+    # the mix really batched and overlapped: some batch was launched (on
+    # another slot, as a slot runs one batch at a time) before an earlier
+    # batch had been seen to complete
     assert max(int(c["batch_size"]) for c in comps) > 1
     assert st["batches"] < n_req
+    spans = {}
+    for c in comps:
+        t0, t1 = float(c["t_dispatch"]), float(c["t_done"])
+        spans[t0] = max(spans.get(t0, t1), t1)
+    order = sorted(spans.items())
+    in_flight = max(sum(1 for t0, t1 in order if t0 <= d < t1) for d, _ in order)
+    assert len(order) == st["batches"]
+    assert in_flight >= 2, "no two batches were ever in flight at once"
     # every request against the oracle: embeds byte for byte with changed
     # and sse, extracts against the oracle's extraction of the same stego
     O = oracle.load()
@@ -170,3 +180,61 @@ def test_server_config_errors(S):
         kw.update(cfg)
         with pytest.raises(S.StegoError):
             S.Server(**kw)
+
+
+def test_paper_layout_requests(S):
+    """Requests in the paper's layout (Sections VI/VII: one plane, two bits
+    per byte, out-of-band length) carry their geometry and are served mixed
+    with one-bit stream requests; every result equals the oracle's."""
+    O = oracle.load()
+    rng = np.random.default_rng(33)
+    geoms = [(1920, 12, 3, 0), (33, 7, 3, 2), (64, 16, 4, 3), (1024, 3, 1, 0), (9, 4, 3, 1)]
+    recs, want, keep = [], [], []
+    for i in range(40):
+        W, H, ch, pl = geoms[i % len(geoms)]
+        n = W * H * ch
+        cov = rng.integers(0, 256, n, dtype=np.uint8)
+        N = int(rng.integers(1, (W // 4) * H + 1))
+        msg = rng.integers(0, 256, N, dtype=np.uint8)
+        c = torch.from_numpy(cov).cuda()
+        m = torch.from_numpy(msg).cuda()
+        st, w = O.paper2_embed(cov, W, H, ch, pl, msg)
+        assert st == 0
+        geo = dict(width=W, height=H, channels=ch, plane=pl)
+        if i % 2 == 0:
+            o = torch.full((n,), 0x5A, dtype=torch.uint8, device="cuda")
+            recs.append(dict(op=S.OP_EMBED, flags=S.LAYOUT_PAPER2, cover=c, stego=o, msg=m,
+                             cover_bytes=n, msg_bytes=N, **geo))
+            want.append(("embed", o, w, O.changed_bytes(cov, w), N))
+        else:
+            stg = torch.from_numpy(w).cuda()
+            o = torch.full((N + 3,), 0xEE, dtype=torch.uint8, device="cuda")
+            recs.append(dict(op=S.OP_EXTRACT, flags=S.LAYOUT_PAPER2, cover=stg, msg=o,
+                             cover_bytes=n, msg_bytes=N + 3, msg_len=N, **geo))
+            want.append(("extract", o, msg, None, N))
+            keep.append(stg)
+        keep += [c, m, o]
+        # a one-bit stream request between the paper-layout ones
+        cs = torch.from_numpy(rng.integers(0, 256, 4096, dtype=np.uint8)).cuda()
+        ms = torch.from_numpy(rng.integers(0, 256, 100, dtype=np.uint8)).cuda()
+        os_ = torch.empty_like(cs)
+        keep += [cs, ms, os_]
+        recs.append(dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=cs, stego=os_, msg=ms,
+                         cover_bytes=4096, msg_bytes=100))
+    srv = S.Server(slots=3, max_batch=16, budget_bytes=1 << 32)
+    arrivals = synth.poisson_arrivals(100000.0, len(recs), 5)
+    # the open-loop runner tags completion k with request index k: paper
+    # request i is request 2i, the stream request after it 2i + 1
+    comps = _by_tag(srv.run_open_loop(S.Server.requests(recs), arrivals, timeout_s=60))
+    srv.close()
+    for i, (kind, o, w, stats, N) in enumerate(want):
+        c = comps[2 * i]
+        assert int(c["status"]) == 0 and int(c["msg_bytes"]) == N, (i, c)
+        got = o.cpu().numpy()
+        if kind == "embed":
+            assert np.array_equal(got, w), i
+            assert (int(c["changed"]), int(c["sse"])) == stats, i
+        else:
+            assert np.array_equal(got[:N], w) and np.all(got[N:] == 0xEE), i
+    assert all(int(comps[2 * i + 1]["status"]) == 0 and int(comps[2 * i + 1]["msg_bytes"]) == 100
+               for i in range(40))
