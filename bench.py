@@ -40,13 +40,14 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_write.sum) from one ncu capture on this exact workload, per
 # kernel family, valid only while the kernel sources hash to `src_sha`.
 # Writes still dirty in the L2 when the kernel exits are not in the count.
-NCU_TRAFFIC = {"embed_vec": {"src_sha": "b72ea941b4dfa871", "bytes": 226528512 + 144812288},
+NCU_TRAFFIC = {"embed_vec": {"src_sha": "d129c172211290e9", "bytes": 226519296 + 145171968},
                "embed_bulk": {"src_sha": "c5b02751867fd4e8", "bytes": 226599680 + 142849024}}
 # The same counters for one launch in the middle of the steady-state
-# sequence (back-to-back launches over distinct buffers, no flush): the
-# previous launches' deferred write-backs land in it as its own do in the
-# next ones, so it counts about one launch's full traffic.
-NCU_TRAFFIC_STEADY = {}
+# sequence (back-to-back launches over distinct buffers, no flush; ncu with
+# --cache-control none): the previous launches' deferred write-backs land in
+# it as its own do in the next ones, so it counts one launch's full traffic.
+NCU_TRAFFIC_STEADY = {"embed_vec": {"src_sha": "d129c172211290e9",
+                                    "bytes": 226527232 + 200964864}}
 KERNEL_SOURCES = ("s1_device.cuh", "stream1.cu", "bulk.cu", "internal.cuh")
 MAX_RING = 192 * 1024
 
@@ -206,6 +207,8 @@ def run_ours(args, rank, world, local_rank):
                             "best_register_us": round(min(t for s_, t in table if not s_[3]), 2),
                             "best_staged_us": round(min(staged), 2) if staged else None}
 
+    if args.profile_case:
+        return run_profile_case(S, torch, dev, synth, args.profile_case)
     if args.steady_only:
         return {"steady_only": run_steady_leg(S, torch, dev, stream, cover, msg, C, m,
                                               max(args.steady_pairs, 2)),
@@ -278,12 +281,20 @@ def run_ours(args, rank, world, local_rank):
         e2e["explicit_copy"] = run_e2e(args, S, torch, dev, stream, cover, msg, C, m)
     # ---- batched vs one launch per image -----------------------------------------
     legs = {}
+    if world > 1 and not args.no_batched:
+        # every rank takes part: the 4096-cover batch split by byte volume
+        sharded = run_sharded_leg(S, AT, torch, dev, stream, synth, rank, world,
+                                  count=args.uneven_count or None)
+        if sharded:
+            legs["batched_uneven_sharded"] = sharded
+        torch.cuda.empty_cache()
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
                                                          "batched_video_paper2", "paper2",
                                                          "streamk", "serving", "small",
                                                          "extract_gather",
                                                          "batched_uneven_host",
-                                                         "batched_uneven_misaligned"}
+                                                         "batched_uneven_misaligned",
+                                                         "single_misaligned"}
     if args.no_batched:
         want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk",
                  "batched_uneven_host", "batched_uneven_misaligned"}
@@ -303,6 +314,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if rank == 0 and "extract_gather" in want:
         legs["extract_gather"] = run_extract_gather_leg(S, AT, torch, dev, synth)
+        torch.cuda.empty_cache()
+    if rank == 0 and "single_misaligned" in want:
+        legs["single_misaligned"] = run_misaligned_leg(S, AT, torch, dev, synth)
         torch.cuda.empty_cache()
     if rank == 0 and "small" in want:
         legs["small_512x512x3"] = run_small_leg(S, AT, torch, dev, synth)
@@ -685,6 +699,95 @@ def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None):
             "outputs_identical_to_aligned": same}
 
 
+def run_sharded_leg(S, AT, torch, dev, stream, synth, rank, world, count=None):
+    """The 4096-cover uneven batch split among the ranks by byte volume
+    (stego_partition): every rank embeds (fused statistics) and extracts its
+    own covers in one batched launch each; no data crosses between GPUs and
+    only the per-cover results are gathered on the host afterwards.  Each
+    timed call starts after a barrier; the time is the slowest rank's."""
+    import torch.distributed as dist
+
+    from paper_0912_0947_gb300 import shard
+    items = synth.uneven_batch(count or 4096)
+    sizes = [it.cover_bytes for it in items]
+    mlens = [it.msg_bytes for it in items]
+    n = len(sizes)
+    off, moff, p, q = [], [], 0, 0
+    for c, m in zip(sizes, mlens):
+        off.append(p)
+        moff.append(q)
+        p += (c + 255) // 256 * 256
+        q += (m + 255) // 256 * 256
+    # every rank generates the same arena and works on its own covers
+    covers = synth.uniform_bytes(p, synth.substream(synth.SEED_BASE + 4, 1), dev)
+    msgs = synth.uniform_bytes(q, synth.substream(synth.SEED_BASE + 4, 2), dev)
+    stego = torch.empty_like(covers)
+    out = torch.zeros_like(msgs)
+    mine = shard.my_covers(sizes, rank, world)
+    k = len(mine)
+    d_e = S.descs_to_device(S.pack_descs(
+        [dict(cover=covers[off[i]:off[i] + sizes[i]], stego=stego[off[i]:off[i] + sizes[i]],
+              msg=msgs[moff[i]:moff[i] + mlens[i]], cover_bytes=sizes[i], msg_bytes=mlens[i],
+              flags=S.HEADER_BE32) for i in mine]), dev)
+    d_x = S.descs_to_device(S.pack_descs(
+        [dict(cover=stego[off[i]:off[i] + sizes[i]], msg=out[moff[i]:moff[i] + mlens[i]],
+              cover_bytes=sizes[i], msg_bytes=mlens[i], flags=S.HEADER_BE32) for i in mine]), dev)
+    res_e = S.new_result(dev, n=max(k, 1))
+    res_x = S.new_result(dev, n=max(k, 1))
+    ws = torch.empty(S.stego_batched_workspace_bytes(max(k, 1)), dtype=torch.uint8, device=dev)
+    flush = AT.Flusher(dev)
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            flush()
+            torch.cuda.synchronize(dev)
+            dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(max_over_ranks(e0.elapsed_time(e1), world, dev))
+        return sorted(ts)[len(ts) // 2]
+
+    emb = lambda: S.stego_embed_batched(d_e, k, res_e, S.FUSE_STATS, ws, stream=stream) if k else None
+    ext = lambda: S.stego_extract_batched(d_x, k, res_x, 0, ws, stream=stream) if k else None
+    emb()
+    ext()
+    t_e = timed(emb)
+    t_x = timed(ext)
+    re = S.read_result(res_e)[:k] if k else []
+    rx = S.read_result(res_x)[:k] if k else []
+    ok_local = all(r["status"] == 0 for r in re + rx) and all(
+        torch.equal(out[moff[i]:moff[i] + mlens[i]], msgs[moff[i]:moff[i] + mlens[i]])
+        for i in mine)
+    gathered = shard.gather_results(mine, [(r["status"], r["changed"], r["sse"]) for r in re], n)
+    oks = [None] * world
+    dist.all_gather_object(oks, ok_local)
+    _, rank_bytes = S.stego_partition(sizes, world)
+    total = sum(sizes)
+    if rank != 0:
+        return None
+    assert all(oks) and all(g is not None and g[0] == 0 for g in gathered),         "sharded batch failed"
+    return {"workload": "4096 uneven covers as in batched_uneven, split among %d GPUs by byte "
+                        "volume (stego_partition), one batched launch per GPU" % world,
+            "ranks": world, "cover_bytes": total,
+            "rank_cover_bytes": [int(b) for b in rank_bytes],
+            "imbalance_bytes": int(rank_bytes.max() - rank_bytes.min()),
+            "largest_cover_bytes": max(sizes),
+            "embed_ms_slowest_rank": round(t_e, 3), "extract_ms_slowest_rank": round(t_x, 3),
+            "embed_cover_gbs": round(total / (t_e * 1e-3) / 1e9, 1),
+            "extract_cover_gbs": round(total / (t_x * 1e-3) / 1e9, 1),
+            "scaling": "strong (the same 4096 covers split among the GPUs)",
+            "gathered_changed": int(sum(g[1] for g in gathered))}
+
+
+# launch shape of the server's batched calls: the library's built-in
+# batched default (threads, vectors per thread, CTAs per SM, tile bytes)
+SERVING_TUNE = (256, 4, 0, 65536)
+
+
 def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=1000000, seconds=20.0,
                     saturation_rates=(100000, 200000, 500000, 1000000, 2000000, 3000000,
                                       5000000)):
@@ -744,7 +847,9 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=1000000, secon
         reqs["msg_bytes"] = mb
         arr = synth.poisson_arrivals(float(rate), cnt,
                                      synth.substream(synth.SEED_BASE + 5, 200 + ri))
-        srv = S.Server(slots=8, max_batch=512, budget_bytes=40 << 30, device=dev)
+        # the library's default batched shapes, whatever earlier legs installed
+        srv = S.Server(slots=8, max_batch=512, budget_bytes=40 << 30, device=dev,
+                       tune_embed=SERVING_TUNE, tune_extract=SERVING_TUNE)
         comps = srv.run_open_loop(reqs, arr, timeout_s=600)
         stats = srv.stats()
         srv.close()
@@ -786,6 +891,7 @@ def run_serving_leg(S, AT, torch, dev, synth, rates, max_requests=1000000, secon
     kept = [r for r in results if r["throughput_req_per_s"] >= 0.9 * r["offered_req_per_s"]]
     return {"workload": "Poisson open loop, 70% embed / 30% extract, 4096 resident uneven "
                         "covers and stegos, 40 GB in-flight budget, 8 slots, batches <= 512",
+            "launch": {"embed": SERVING_TUNE, "extract": SERVING_TUNE},
             "per_rate": "max(500, min(%d, rate x %g s)) requests, a new server per rate" % (
                 max_requests, seconds),
             "rates": results,
@@ -1040,6 +1146,74 @@ def run_steady_leg(S, torch, dev, stream, cover, msg, C, m, pairs, rounds=5):
                         "sets (%.1f GB), no flush between them; one event interval" % (
                             pairs, pairs * (2 * C + m) / 1e9)})
     return out
+
+
+MISALIGNED_CASES = ((0, 0, 0), (3, 3, 0), (5, 5, 1), (3, 7, 0), (0, 8, 0), (12, 4, 1))
+
+
+def misaligned_views(S, torch, dev, w, co, so, mo):
+    """The 8192x8192x3 cover (less 16 bytes) and its message placed co, so
+    and mo bytes past 256-byte aligned allocations: cover, stego and
+    message at those misalignments, the message at full capacity."""
+    C, m = w.cover_bytes, w.msg_bytes
+    Cm = C - 16
+    mm = Cm // 8 - 4
+    bufs = [torch.empty(C + 64, dtype=torch.uint8, device=dev) for _ in range(2)] + \
+        [torch.empty(m + 64, dtype=torch.uint8, device=dev) for _ in range(2)]
+    cv, sv = bufs[0][co:co + Cm], bufs[1][so:so + Cm]
+    mv, ov = bufs[2][mo:mo + mm], bufs[3][mo:mo + mm]
+    cv.copy_(w.cover(dev)[:Cm])
+    mv.copy_(w.message(dev)[:mm])
+    return bufs, cv, sv, mv, ov, Cm, mm
+
+
+def run_misaligned_leg(S, AT, torch, dev, synth):
+    """Single-cover embed (fused statistics) and extract of the 201 MB cover
+    with the cover, stego and message at several misalignments (cover
+    offset, stego offset, message offset from a 16-byte boundary): same
+    offset (vectors after a scalar head), different offsets (stego vectors
+    joined from cover vector pairs), and the extract of a misaligned stego;
+    each against the aligned case, outputs compared with it."""
+    w = synth.single_8192()
+    flush = AT.Flusher(dev)
+    peak, _ = hbm_peak()
+    res = S.new_result(dev)
+    ref = None
+    out = {}
+    for co, so, mo in MISALIGNED_CASES:
+        bufs, cv, sv, mv, ov, Cm, mm = misaligned_views(S, torch, dev, w, co, so, mo)
+        fe = lambda: S.stego_embed(cv, sv, mv, S.HEADER_BE32 | S.FUSE_STATS, res)
+        fx = lambda: S.stego_extract(sv, ov, 0, S.HEADER_BE32, res)
+        te = AT.time_call(fe, flush, 15)
+        tx = AT.time_call(fx, flush, 15)
+        torch.cuda.synchronize(dev)
+        if ref is None:
+            ref = sv.clone()
+        assert torch.equal(sv, ref) and torch.equal(ov, mv), "misaligned outputs differ"
+        T = 8 * (mm + 4)
+        out["c%d_s%d_m%d" % (co, so, mo)] = {
+            "embed_us": round(te, 2), "embed_frac": round((2 * Cm + T // 8) / (te * 1e-6) / 1e9
+                                                          / peak, 4),
+            "extract_us": round(tx, 2), "extract_frac": round((T + T // 8) / (tx * 1e-6) / 1e9
+                                                              / peak, 4)}
+        del bufs
+    return {"workload": "8192x8192x3 cover less 16 bytes at full capacity; key c<cover>_s<stego>"
+                        "_m<message> = byte offsets from a 16-byte boundary", "cases": out}
+
+
+def run_profile_case(S, torch, dev, synth, spec):
+    """--profile-case co,so,mo: one warm-up and one more embed + extract of
+    the misaligned case (for a profiler); prints nothing but a check."""
+    co, so, mo = (int(x) for x in spec.split(","))
+    w = synth.single_8192()
+    bufs, cv, sv, mv, ov, Cm, mm = misaligned_views(S, torch, dev, w, co, so, mo)
+    res = S.new_result(dev)
+    for _ in range(2):
+        S.stego_embed(cv, sv, mv, S.HEADER_BE32 | S.FUSE_STATS, res)
+        S.stego_extract(sv, ov, 0, S.HEADER_BE32, res)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(ov, mv)
+    return {"profile_case": spec, "ok": True}
 
 
 def tune_dict(t):
@@ -1425,6 +1599,9 @@ def main():
                     help="distinct cover/stego sets of the steady-state leg (0: skip)")
     ap.add_argument("--steady-only", action="store_true",
                     help="run only the steady-state sequence (for an ncu capture)")
+    ap.add_argument("--profile-case", default="",
+                    help="co,so,mo: run only two embed + extract calls of the 201 MB cover "
+                         "at those byte offsets (for an ncu capture)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1446,7 +1623,7 @@ def main():
     ap.add_argument("--legs", default="",
                     help="comma list of extra legs: batched_uneven,batched_video,"
                          "batched_video_paper2,paper2,streamk,serving,small,extract_gather,"
-                         "batched_uneven_host,batched_uneven_misaligned, "
+                         "batched_uneven_host,batched_uneven_misaligned,single_misaligned, "
                          "or none "
                          "(default all)")
     args = ap.parse_args()

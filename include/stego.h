@@ -546,6 +546,25 @@ int stego_pipeline_extract(stego_pipeline *p, const stego_host_job *jobs, uint32
  * staging (not the arena). */
 int stego_pipeline_destroy(stego_pipeline *p);
 
+/* ------------------------------------------------------------------ */
+/* Several GPUs: splitting a batch by byte volume                       */
+/* ------------------------------------------------------------------ */
+/* Covers are independent (the paper repeats its routine per row and per
+ * frame, Section VI, last paragraph), so a batch shards across `world` GPUs
+ * with no exchange step: each GPU runs the batched calls on its own covers
+ * and only the per-cover results are gathered.  This call assigns covers
+ * to GPUs by byte volume: covers in decreasing size (ties by index), each
+ * to the GPU with the fewest bytes so far (ties to the lowest rank), so
+ * every GPU ends within one cover's bytes of every other.  Host only: no
+ * CUDA call, no device memory.
+ *   bytes       host array of n cover sizes (the work of each cover).
+ *   rank_of     host array of n: the GPU (0..world-1) of each cover.
+ *   rank_bytes  optional host array of world: bytes assigned to each GPU.
+ * Returns STEGO_OK, or STEGO_E_INVAL for world == 0 or a null array with
+ * n > 0. */
+int stego_partition(const uint64_t *bytes, uint32_t n, uint32_t world, uint32_t *rank_of,
+                    uint64_t *rank_bytes);
+
 /* Where a buffer lives, as the CUDA runtime of the current device reports
  * it, and whether this library's kernels may read and write it directly.
  *   *kind: STEGO_MEM_PAGEABLE (ordinary host memory), STEGO_MEM_PINNED

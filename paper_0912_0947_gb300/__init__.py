@@ -184,6 +184,8 @@ def lib() -> ctypes.CDLL:
         L.stego_pipeline_extract.restype = _int
         L.stego_pipeline_destroy.argtypes = [_vp]
         L.stego_pipeline_destroy.restype = _int
+        L.stego_partition.argtypes = [_vp, _u32, _u32, _vp, _vp]
+        L.stego_partition.restype = _int
         L.stego_test_bounded_wait.argtypes = [_u64, _u32]
         L.stego_test_bounded_wait.restype = _int
         L.stego_set_tune.argtypes = [_int, ctypes.POINTER(Tune)]
@@ -395,6 +397,18 @@ def stego_pointer_kind(ptr: int):
     _check(lib().stego_pointer_kind(_vp(ptr), ctypes.byref(k), ctypes.byref(a)),
            "stego_pointer_kind")
     return k.value, bool(a.value)
+
+
+def stego_partition(sizes, world: int):
+    """(rank of each cover, bytes of each rank): covers split among `world`
+    GPUs by byte volume (stego_partition)."""
+    b = np.ascontiguousarray(np.asarray(sizes, dtype=np.uint64))
+    rank_of = np.zeros(max(len(b), 1), dtype=np.uint32)
+    rank_bytes = np.zeros(max(int(world), 1), dtype=np.uint64)
+    _check(lib().stego_partition(b.ctypes.data if len(b) else None, len(b), int(world),
+                                 rank_of.ctypes.data, rank_bytes.ctypes.data),
+           "stego_partition")
+    return rank_of[: len(b)], rank_bytes[: int(world)]
 
 
 def stego_test_bounded_wait(limit_ns: int, withhold_arrival: int) -> None:

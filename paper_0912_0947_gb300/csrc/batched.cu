@@ -15,10 +15,10 @@
 //                current chunk is processed), find the owning descriptor by
 //                binary search over the offsets once per chunk, and run the
 //                same per-vector code as the single-cover kernels on each
-//                tile; two persistent kernels: one for the one-bit stream on
-//                16-byte aligned buffers, one for the paper layout's tiles and
-//                then the one-bit stream on misaligned buffers (each space
-//                exits at once when it is empty).
+//                tile; one persistent kernel per tile space (one-bit stream
+//                on 16-byte aligned buffers, one-bit stream on misaligned
+//                buffers, paper layout), each exiting at once when its space
+//                is empty.
 // Workspace (caller-owned scratch, 16-byte aligned):
 //   [0, 64)                 head: tile totals and work counters
 //   [64, 64 + 24(n+1))      tile offsets of the three spaces (counts before
@@ -731,16 +731,51 @@ __device__ __forceinline__ void mis_extract_tile(const stego_desc &D, const Desc
             s1::extract_one(x, x.len - 1);
 }
 
-// The second persistent kernel of a batched call: the paper layout's tiles
-// (units, rows or runs), then the misaligned stream tiles, each claimed like
-// above.  A register budget apart from the aligned stream kernel's, and one
-// launch for both spaces (an empty space costs one claim).  Capped at 80
-// registers for three CTAs per SM: on 600 video frames the paper-layout
+// The misaligned stream tiles' own persistent kernels, so that a misaligned
+// batch keeps 32 warps per SM (inside the paper layout's 80-register kernel
+// it ran with 24: 4096 covers, embed 0.69 of the HBM peak there, 0.75 here).
+// The embed runs 512 threads per CTA, the extract 256 (a 64 KiB tile is four
+// rounds of its warps instead of two: 0.87 against 0.76 of the peak).
+constexpr int kMisEmbedThreads = 512, kMisExtractThreads = 256;
+template <bool STATS>
+__global__ void __launch_bounds__(512) persist_mis_embed(const stego_desc *descs, uint32_t n,
+                                                         stego_result *results, WsView ws)
+{
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
+    unsigned long long changed = 0, sse = 0;
+    uint32_t stat_d = 0xFFFFFFFFu;
+    claim_loop(ws.start_m, ws.head->total_m, &ws.head->counter_m, n,
+               [&](uint32_t d, unsigned long long lt) {
+        if (STATS && d != stat_d) {
+            flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+            stat_d = d;
+        }
+        mis_embed_tile<STATS>(descs[d], ws.info[d], lt, changed, sse);
+    });
+    if (STATS)
+        flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
+}
+
+__global__ void __launch_bounds__(256) persist_mis_extract(const stego_desc *descs, uint32_t n,
+                                                           WsView ws)
+{
+    grid_dependency_wait(); // launched dependent: nothing is touched before
+    allow_dependents();
+    claim_loop(ws.start_m, ws.head->total_m, &ws.head->counter_m, n,
+               [&](uint32_t d, unsigned long long lt) {
+        mis_extract_tile(descs[d], ws.info[d], lt);
+    });
+}
+
+// The paper layout's own persistent kernels (a separate register budget from
+// the stream kernels): tiles of units, rows or runs, claimed like above.
+// Capped at 80 registers for three CTAs per SM: on 600 video frames the
 // embed with statistics went from 1.47 to 1.32 ms and the extract from 0.54
 // to 0.48 ms, although the statistics variant spills (120 bytes).
 template <bool STATS>
-__global__ void __launch_bounds__(256, 3) persist_aux_embed(const stego_desc *descs, uint32_t n,
-                                                         stego_result *results, WsView ws)
+__global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *descs, uint32_t n,
+                                                        stego_result *results, WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
     allow_dependents();
@@ -754,30 +789,18 @@ __global__ void __launch_bounds__(256, 3) persist_aux_embed(const stego_desc *de
         }
         paper_embed_tile<STATS>(descs[d], ws.info[d], lt, changed, sse);
     });
-    claim_loop(ws.start_m, ws.head->total_m, &ws.head->counter_m, n,
-               [&](uint32_t d, unsigned long long lt) {
-        if (STATS && d != stat_d) {
-            flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
-            stat_d = d;
-        }
-        mis_embed_tile<STATS>(descs[d], ws.info[d], lt, changed, sse);
-    });
     if (STATS)
         flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
 }
 
-__global__ void __launch_bounds__(256, 3) persist_aux_extract(const stego_desc *descs, uint32_t n,
-                                                           WsView ws)
+__global__ void __launch_bounds__(256, 3) persist_p2_extract(const stego_desc *descs, uint32_t n,
+                                                          WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
     allow_dependents();
     claim_loop(ws.start_p, ws.head->total_p, &ws.head->counter_p, n,
                [&](uint32_t d, unsigned long long lt) {
         paper_extract_tile(descs[d], ws.info[d], lt);
-    });
-    claim_loop(ws.start_m, ws.head->total_m, &ws.head->counter_m, n,
-               [&](uint32_t d, unsigned long long lt) {
-        mis_extract_tile(descs[d], ws.info[d], lt);
     });
 }
 
@@ -859,12 +882,28 @@ int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint
     }
     if (e != cudaSuccess)
         return STEGO_E_CUDA;
-    // paper-layout and misaligned stream tiles (their counts are on the
-    // device; empty spaces exit at once)
+    // misaligned stream tiles (count on the device; an empty set exits at once)
+    {
+        const int mis_threads = EMBED ? kMisEmbedThreads : kMisExtractThreads;
+        const void *km = EMBED ? (stats ? (const void *)persist_mis_embed<true>
+                                        : (const void *)persist_mis_embed<false>)
+                               : (const void *)persist_mis_extract;
+        const int gridm = persistent_grid(km, mis_threads, 0, 0, ~0ull >> 1, 1);
+        if (EMBED) {
+            void *args[] = {(void *)&d_descs, &n, &d_results, &ws};
+            e = launch_dependent(km, dim3(gridm), dim3(mis_threads), args, 0, s);
+        } else {
+            void *args[] = {(void *)&d_descs, &n, &ws};
+            e = launch_dependent(km, dim3(gridm), dim3(mis_threads), args, 0, s);
+        }
+    }
+    if (e != cudaSuccess)
+        return STEGO_E_CUDA;
+    // paper-layout tiles (their count is on the device; an empty set exits at once)
     const int p2_threads = 256;
-    const void *kp = EMBED ? (stats ? (const void *)persist_aux_embed<true>
-                                    : (const void *)persist_aux_embed<false>)
-                           : (const void *)persist_aux_extract;
+    const void *kp = EMBED ? (stats ? (const void *)persist_p2_embed<true>
+                                    : (const void *)persist_p2_embed<false>)
+                           : (const void *)persist_p2_extract;
     const int gridp = persistent_grid(kp, p2_threads, 0, 0, ~0ull >> 1, 1);
     if (EMBED) {
         void *args[] = {(void *)&d_descs, &n, &d_results, &ws};

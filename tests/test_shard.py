@@ -1,0 +1,106 @@
+"""Several GPUs, host side (CPU): the byte-volume partition of a batch
+(stego_partition) and the sharded runner's gather, with two gloo ranks on
+the CPU.  The per-cover work in the gloo test is the oracle's embed (there
+is no GPU here); the point is the host logic: every cover on exactly one
+rank, the ranks within one cover's bytes of each other, and the gathered
+per-cover results equal to one process's over the whole batch."""
+import json
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import paper_0912_0947_gb300 as S
+from paper_0912_0947_gb300 import shard, synth
+
+
+def test_partition_balanced_within_one_cover():
+    items = synth.uneven_batch(4096)
+    sizes = np.array([it.cover_bytes for it in items], dtype=np.uint64)
+    for world in (1, 2, 3, 4, 7, 8):
+        rank_of, rank_bytes = S.stego_partition(sizes, world)
+        assert rank_of.shape == (4096,) and rank_of.max() < world
+        loads = np.bincount(rank_of, weights=sizes.astype(np.float64), minlength=world)
+        assert np.array_equal(loads.astype(np.uint64), rank_bytes)
+        assert int(rank_bytes.sum()) == int(sizes.sum())
+        assert int(rank_bytes.max() - rank_bytes.min()) <= int(sizes.max())
+        # deterministic: the same split every time
+        assert np.array_equal(S.stego_partition(sizes, world)[0], rank_of)
+        parts = [shard.my_covers(sizes, r, world) for r in range(world)]
+        assert sorted(np.concatenate(parts).tolist()) == list(range(4096))
+
+
+def test_partition_small_cases():
+    # largest first, each to the least-loaded rank (ties to the lower rank)
+    rank_of, rank_bytes = S.stego_partition([5, 9, 1, 7, 3, 3], 2)
+    assert rank_of.tolist() == [1, 0, 1, 1, 0, 0] and rank_bytes.tolist() == [15, 13]
+    rank_of, rank_bytes = S.stego_partition([], 3)
+    assert rank_of.size == 0 and rank_bytes.tolist() == [0, 0, 0]
+    rank_of, rank_bytes = S.stego_partition([4, 4], 5)  # more ranks than covers
+    assert rank_of.tolist() == [0, 1] and rank_bytes.tolist() == [4, 4, 0, 0, 0]
+    with pytest.raises(S.StegoError) as e:
+        S.stego_partition([1, 2], 0)
+    assert e.value.status == S.E_INVAL
+
+
+def _batch():
+    items = synth.uneven_batch(48, lo=16, hi=300)
+    rng = np.random.default_rng(5)
+    covers = [rng.integers(0, 256, it.cover_bytes, dtype=np.uint8) for it in items]
+    msgs = [rng.integers(0, 256, it.msg_bytes, dtype=np.uint8) for it in items]
+    return [it.cover_bytes for it in items], covers, msgs
+
+
+def _compute(idx):
+    import oracle
+    O = oracle.load()
+    _, covers, msgs = _batch()
+    out = []
+    for i in idx:
+        st, w = O.stream1_embed(covers[i], msgs[i], header=True)
+        ch, sse = O.changed_bytes(covers[i], w)
+        out.append({"status": st, "changed": ch, "sse": sse, "sum": int(w.sum(dtype=np.uint64))})
+    return out
+
+
+def _rank_main(rank, world, port, path):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    sizes, _, _ = _batch()
+    got = shard.run_sharded(sizes, rank, world, _compute)
+    mine = shard.my_covers(sizes, rank, world).tolist()
+    if rank == 0:
+        with open(path, "w") as f:
+            json.dump({"results": got}, f)
+    with open(path + ".rank%d" % rank, "w") as f:
+        json.dump(mine, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def test_sharded_two_gloo_ranks_equal_one_process(tmp_path):
+    path = str(tmp_path / "gathered.json")
+    mp.spawn(_rank_main, args=(2, _free_port(), path), nprocs=2, join=True)
+    with open(path) as f:
+        got = json.load(f)["results"]
+    sizes, _, _ = _batch()
+    want = _compute(range(len(sizes)))
+    assert got == want
+    # the two ranks' shares are disjoint, cover everything and balance bytes
+    shares = [json.load(open(path + ".rank%d" % r)) for r in range(2)]
+    assert sorted(shares[0] + shares[1]) == list(range(len(sizes)))
+    b = [sum(sizes[i] for i in sh) for sh in shares]
+    assert abs(b[0] - b[1]) <= max(sizes)
+    # one process, no collective: the same results
+    assert shard.run_sharded(sizes, 0, 1, _compute) == want
