@@ -418,6 +418,7 @@ def run_ours(args, rank, world, local_rank):
             "traffic_steady": rec_s["bytes"] if rec_s and rec_s["src_sha"] == sha else None,
             "steady": dict(steady, embed_frac=round(st_emb / peak, 4),
                            extract_frac=round(st_ext / peak, 4),
+                           embed_frac_of_copy=round(st_emb / steady["copy_gbs"], 4),
                            regime="steady state: back-to-back launches, every write-back "
                                   "inside the timed interval")})
     if e2e:
@@ -1138,6 +1139,24 @@ def run_steady_leg(S, torch, dev, stream, cover, msg, C, m, pairs, rounds=5):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         out[name + "_us"] = round(e0.elapsed_time(e1) * 1e3 / (rounds * pairs), 2)
+    # the same back-to-back sequence as a plain device copy of each cover
+    # into its stego (torch copy_, 2C bytes per launch): the practical
+    # ceiling of a read + write stream in this regime
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(pairs):
+        stegos[k].copy_(covers[k])
+    e0.record(stream)
+    for _ in range(rounds):
+        for k in range(pairs):
+            stegos[k].copy_(covers[k])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    out["copy_us"] = round(e0.elapsed_time(e1) * 1e3 / (rounds * pairs), 2)
+    out["copy_gbs"] = round(2 * C / (out["copy_us"] * 1e-6) / 1e9, 1)
+    for k in range(pairs):  # the stegos again, for the round-trip check
+        emb(k)
+        ext(k)
+    torch.cuda.synchronize(dev)
     rr = S.read_result(res)
     assert all(r["status"] == 0 and r["msg_bytes"] == m for r in rr)
     assert all(torch.equal(o, msg) for o in outs), "steady-state round trip differs"

@@ -83,6 +83,14 @@ def test_autotune_picks_restores_and_caches(tmp_path, monkeypatch):
         return abs(t.threads - 256) / 64 + abs(t.vec_per_thread - 8) + abs(t.ctas_per_sm - 2) + 10.0
 
     monkeypatch.setattr(AT, "time_call", fake_time)
+    b2b = []
+
+    def fake_b2b(fn, reps=10, stream=None):
+        t = S.stego_get_tune(S.OP_EXTRACT)
+        b2b.append((t.threads, t.vec_per_thread, t.ctas_per_sm, t.tile_bytes))
+        return 1.0
+
+    monkeypatch.setattr(AT, "time_back_to_back", fake_b2b)
     old = S.stego_get_tune(S.OP_EXTRACT)
     try:
         best, us, table = AT.autotune(S.OP_EXTRACT, lambda: None, 1 << 27, flush=lambda: None,
@@ -93,6 +101,8 @@ def test_autotune_picks_restores_and_caches(tmp_path, monkeypatch):
         assert (t.threads, t.vec_per_thread, t.ctas_per_sm, t.tile_bytes) == (256, 8, 2, 0)
         assert len(set(seen)) == n_cand  # every candidate installed, staged ones included
         assert {x[3] for x in seen} == {0, 65536, 131072}
+        # a unique fastest shape needs no back-to-back comparison
+        assert b2b == []
         S.stego_set_tune(S.OP_EXTRACT, (128, 2, 0, 0))
         hit = AT.load_cached(S.OP_EXTRACT, 1 << 27)  # same size class: cached and installed
         assert hit["shape"][:3] == [256, 8, 2]
@@ -101,3 +111,42 @@ def test_autotune_picks_restores_and_caches(tmp_path, monkeypatch):
         assert AT.load_cached(S.OP_EXTRACT, 1 << 20) is None  # other size class
     finally:
         S.stego_set_tune(S.OP_EXTRACT, old)
+
+
+def test_autotune_tie_break_back_to_back(tmp_path, monkeypatch):
+    """Shapes within 1.5% of the fastest flushed time are told apart back to
+    back; shapes further away are never tried that way."""
+    import paper_0912_0947_gb300 as S
+    from paper_0912_0947_gb300 import autotune as AT
+    from paper_0912_0947_gb300 import build as B
+    try:
+        B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    B.build()
+    monkeypatch.setenv("STEGO_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=None: "FakeGPU")
+    flushed = {(128, 2, 0, 0): 65.5, (256, 2, 0, 0): 65.6, (512, 8, 0, 0): 65.4,
+               (128, 8, 0, 0): 80.0}
+    steady = {(128, 2, 0, 0): 74.0, (256, 2, 0, 0): 70.0, (512, 8, 0, 0): 75.0,
+              (128, 8, 0, 0): 60.0}
+    cur = lambda: tuple(getattr(S.stego_get_tune(S.OP_EMBED), f)
+                        for f in ("threads", "vec_per_thread", "ctas_per_sm", "tile_bytes"))
+    tried = []
+    monkeypatch.setattr(AT, "time_call", lambda fn, flush, reps=15, stream=None: flushed[cur()])
+
+    def b2b(fn, reps=10, stream=None):
+        tried.append(cur())
+        return steady[cur()]
+
+    monkeypatch.setattr(AT, "time_back_to_back", b2b)
+    old = S.stego_get_tune(S.OP_EMBED)
+    try:
+        best, us, table = AT.autotune(S.OP_EMBED, lambda: None, 1 << 27,
+                                      candidates=list(flushed), flush=lambda: None,
+                                      use_cache=False)
+        assert best == (256, 2, 0, 0) and us == 65.6
+        assert sorted(tried) == sorted([(128, 2, 0, 0), (256, 2, 0, 0), (512, 8, 0, 0)])
+        assert cur() == (256, 2, 0, 0)
+    finally:
+        S.stego_set_tune(S.OP_EMBED, old)
