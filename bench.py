@@ -281,6 +281,7 @@ def run_ours(args, rank, world, local_rank):
         e2e["explicit_copy"] = run_e2e(args, S, torch, dev, stream, cover, msg, C, m)
     # ---- batched vs one launch per image -----------------------------------------
     legs = {}
+    uneven_tune = None  # the uneven batch's tuned batched shapes, for its other legs
     if world > 1 and not args.no_batched:
         # every rank takes part: the 4096-cover batch split by byte volume
         sharded = run_sharded_leg(S, AT, torch, dev, stream, synth, rank, world,
@@ -308,6 +309,9 @@ def run_ours(args, rank, world, local_rank):
                 S, AT, torch, dev, stream, synth, kind,
                 count=(args.uneven_count if kind == "uneven" else args.video_frames) or None,
                 tune=not args.no_tune)
+            if kind == "uneven" and legs[("batched_" + kind)]["launch"]:
+                sel = legs["batched_uneven"]["launch"]
+                uneven_tune = (tuple(sel["embed"]), tuple(sel["extract"]))
             torch.cuda.empty_cache()
     if rank == 0 and "streamk" in want:
         legs["streamk"] = run_streamk_leg(S, AT, torch, dev, synth)
@@ -326,11 +330,12 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if rank == 0 and "batched_uneven_misaligned" in want:
         legs["batched_uneven_misaligned"] = run_misaligned_batched_leg(
-            S, AT, torch, dev, stream, synth, count=args.uneven_count or None)
+            S, AT, torch, dev, stream, synth, count=args.uneven_count or None, tune=uneven_tune)
         torch.cuda.empty_cache()
     if rank == 0 and "batched_uneven_host" in want:
         legs["batched_uneven_host"] = run_host_batched_leg(S, torch, dev, synth,
-                                                           count=args.uneven_count or None)
+                                                           count=args.uneven_count or None,
+                                                           tune=uneven_tune)
         torch.cuda.empty_cache()
     if rank == 0 and "serving" in want:
         legs["serving"] = run_serving_leg(S, AT, torch, dev, synth,
@@ -612,7 +617,7 @@ def run_batched_leg(S, AT, torch, dev, stream, synth, kind, count=None, tune=Tru
     }
 
 
-def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None):
+def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None, tune=None):
     """The 4096-cover uneven batch with every cover 1..15 bytes past a
     16-byte boundary and every stego at its own random offset (the funnel
     routine: stego vectors joined from cover vector pairs; same offsets take
@@ -670,8 +675,9 @@ def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None):
     res = S.new_result(dev, n=n)
     ws = torch.empty(S.stego_batched_workspace_bytes(n), dtype=torch.uint8, device=dev)
     flush = AT.Flusher(dev)
-    emb = lambda d: S.stego_embed_batched(d, n, res, S.FUSE_STATS, ws, stream=stream)
-    ext = lambda d: S.stego_extract_batched(d, n, res, 0, ws, stream=stream)
+    te_, tx_ = tune if tune else (None, None)
+    emb = lambda d: S.stego_embed_batched(d, n, res, S.FUSE_STATS, ws, tune=te_, stream=stream)
+    ext = lambda d: S.stego_extract_batched(d, n, res, 0, ws, tune=tx_, stream=stream)
     t = {"misaligned_embed_us": AT.time_call(lambda: emb(d_me), flush, 7),
          "aligned_embed_us": AT.time_call(lambda: emb(d_ae), flush, 7),
          "misaligned_extract_us": AT.time_call(lambda: ext(d_mx), flush, 7),
@@ -689,6 +695,7 @@ def run_misaligned_batched_leg(S, AT, torch, dev, stream, synth, count=None):
                         "a 16-byte boundary, each stego at its own random offset 1..15, "
                         "messages at random parity",
             "covers": n, "cover_bytes": total,
+            "launch": {"embed": te_, "extract": tx_},
             **{k: round(v, 1) for k, v in t.items()},
             "hbm_frac": {"misaligned_embed": frac(emb_bytes, t["misaligned_embed_us"]),
                          "aligned_embed": frac(emb_bytes, t["aligned_embed_us"]),
@@ -1317,7 +1324,7 @@ def run_e2e_library(args, S, torch, dev, cover_d, msg_d, C, m, slots=3):
             "h2d_bytes_per_step": C + m + 72, "d2h_bytes_per_step": C + m + 64}
 
 
-def run_host_batched_leg(S, torch, dev, synth, count=None, slots=3, slot_mb=256):
+def run_host_batched_leg(S, torch, dev, synth, count=None, slots=3, slot_mb=256, tune=None):
     """The 4096 uneven covers of the batched leg held in pinned host memory
     (cover, stego and message arenas), embedded and then extracted through
     the library's host pipeline: copy-in, batched kernels and copy-out of
@@ -1348,7 +1355,9 @@ def run_host_batched_leg(S, torch, dev, synth, count=None, slots=3, slot_mb=256)
                                msg_bytes=mlens[i], flags=S.HEADER_BE32) for i in range(n)])
     modes = {}
     for mode_name, mode in (("staged", S.PIPE_STAGED), ("auto", S.PIPE_AUTO)):
-        pipe = S.Pipeline(slots=slots, max_descs=4096, slot_bytes=slot_mb << 20, mode=mode)
+        te_, tx_ = tune if tune else ((0, 0, 0, 0), (0, 0, 0, 0))
+        pipe = S.Pipeline(slots=slots, max_descs=4096, slot_bytes=slot_mb << 20, mode=mode,
+                          tune_embed=te_, tune_extract=tx_)
         out.zero_()
         stego.zero_()
         pipe.embed(ej[:64], S.FUSE_STATS)  # warm-up
