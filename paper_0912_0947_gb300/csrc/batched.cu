@@ -200,16 +200,16 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
             const p2::View v = p2::make_view(nullptr, nullptr, D.geom.width, D.geom.height, ch,
                                              D.geom.plane, nullptr, nullptr, D.msg_bytes);
             if (!inplace && d_aligned16(D.cover) && d_aligned16(D.stego) &&
-                (ch == 3 || ch == 1) && D.geom.plane == 0 && D.geom.width % 16u == 0 &&
+                (ch == 3 || ch == 1) && D.geom.width % 16u == 0 &&
                 (uint64_t)D.geom.width / 16u * D.geom.height < (1ull << 31)) {
-                // one-pass units for the common planes: RGB plane 0, grayscale
+                // one-pass units: grayscale, or RGB with any plane
                 const uint64_t units = (uint64_t)(D.geom.width / 16u) * D.geom.height;
                 const uint64_t per = tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u;
                 inf.mode = kP2Units;
                 inf.per_tile = (uint32_t)per;
                 tiles = (units + per - 1) / per;
             } else if (inplace && d_aligned16(D.cover) && (ch == 3 || ch == 1) &&
-                       D.geom.plane == 0 && D.geom.width % 16u == 0 &&
+                       D.geom.width % 16u == 0 &&
                        (uint64_t)D.geom.width / 16u * D.geom.height < (1ull << 31)) {
                 // in place: the units of the carrying rows, written back whole
                 const uint64_t units = (uint64_t)(D.geom.width / 16u) * v.R;
@@ -518,6 +518,19 @@ __device__ __forceinline__ void claim_loop(const unsigned long long *start,
     }
 }
 
+struct TileStats {
+    unsigned long long changed, sse;
+};
+
+// The units of one tile of an RGB cover carrying in plane PLANE.
+template <int PLANE, bool STATS>
+__device__ __noinline__ TileStats rgb_units_tile(const p2::View v, uint32_t k0, uint32_t k1)
+{
+    TileStats t{0ull, 0ull};
+    p2::units_embed<3, PLANE, STATS, 1>(v, k0, k1, blockDim.x, t.changed, t.sse);
+    return t;
+}
+
 // One tile of a paper-layout cover (the CTA's threads together).
 template <bool STATS>
 __device__ __forceinline__ void paper_embed_tile(const stego_desc &D, const DescInfo &inf,
@@ -541,10 +554,18 @@ __device__ __forceinline__ void paper_embed_tile(const stego_desc &D, const Desc
         // 80-register cap a form staged through shared memory spilled more
         // and ran slower (600 video frames: 1.53 against 1.26 ms), and so did
         // the cp.async pipeline of the single-cover kernel (1.34-1.83 ms)
-        if (inf.channels == 3)
-            p2::units_embed<3, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
-        else
+        if (inf.channels == 1) {
             p2::units_embed<1, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
+        } else if (inf.plane == 0) {
+            p2::units_embed<3, 0, STATS, 1>(v, k0, k1, blockDim.x, changed, sse);
+        } else {
+            // planes 1 and 2 of RGB in calls of their own, so that their
+            // registers do not crowd the plane-0 path (once per tile)
+            const TileStats t = inf.plane == 1 ? rgb_units_tile<1, STATS>(v, k0, k1)
+                                               : rgb_units_tile<2, STATS>(v, k0, k1);
+            changed += t.changed;
+            sse += t.sse;
+        }
         return;
     }
     const uint32_t r0 = (uint32_t)b0;

@@ -304,7 +304,8 @@ def test_batched_paper_layout_mixed_with_stream(S, O):
     extraction with the out-of-band length."""
     rng = np.random.default_rng(41)
     geoms = [(16, 5, 3, 1), (1920, 9, 3, 0), (33, 7, 3, 2), (64, 16, 4, 3), (1024, 3, 1, 0),
-             (9, 4, 3, 1), (4000, 6, 4, 2), (7, 3, 2, 1), (3, 4, 1, 0)]
+             (9, 4, 3, 1), (4000, 6, 4, 2), (7, 3, 2, 1), (3, 4, 1, 0), (1920, 20, 3, 1),
+             (1920, 30, 3, 2), (512, 40, 3, 2)]
     recs, want, covers, kinds = [], [], [], []
     keep = []
     for gi, (W, H, C, pl) in enumerate(geoms):
