@@ -324,6 +324,7 @@ int stego_embed(const uint8_t *d_cover, uint8_t *d_stego, uint64_t cover_bytes,
                 const uint8_t *d_msg, uint64_t msg_bytes, const stego_geom *geom,
                 uint32_t flags, stego_result *d_result, void *stream)
 {
+    stego::Trace trace_("stego_embed");
     const uint32_t known = STEGO_LAYOUT_MASK | STEGO_HEADER_BE32 | STEGO_FUSE_STATS |
                            STEGO_PLANE_ONLY | STEGO_BITS_MASK;
     if (flags & ~known)
@@ -503,6 +504,7 @@ int stego_extract(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *d_msg,
                   uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom, uint32_t flags,
                   stego_result *d_result, void *stream)
 {
+    stego::Trace trace_("stego_extract");
     return extract_impl(d_stego, cover_bytes, d_msg, msg_cap, msg_len, geom, flags, d_result,
                         stream, false);
 }
@@ -511,6 +513,7 @@ int stego_extract_ballot(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *
                          uint64_t msg_cap, uint64_t msg_len, const stego_geom *geom,
                          uint32_t flags, stego_result *d_result, void *stream)
 {
+    stego::Trace trace_("stego_extract_ballot");
     return extract_impl(d_stego, cover_bytes, d_msg, msg_cap, msg_len, geom, flags, d_result,
                         stream, true);
 }
@@ -518,6 +521,7 @@ int stego_extract_ballot(const uint8_t *d_stego, uint64_t cover_bytes, uint8_t *
 int stego_changed_bytes(const uint8_t *d_a, const uint8_t *d_b, uint64_t n, uint64_t *d_out2,
                         void *stream)
 {
+    stego::Trace trace_("stego_changed_bytes");
     if (!d_out2 || ((uintptr_t)d_out2 & 7u))
         return STEGO_E_INVAL;
     if (n > 0 && (!d_a || !d_b))

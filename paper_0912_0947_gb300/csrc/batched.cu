@@ -954,6 +954,7 @@ int stego_embed_batched(const stego_desc *d_descs, uint32_t n, stego_result *d_r
                         uint32_t flags, const stego_tune *tune, void *d_ws, uint64_t ws_bytes,
                         void *stream)
 {
+    stego::Trace trace_("stego_embed_batched");
     return batched<true>(d_descs, n, d_results, flags, tune, d_ws, ws_bytes, stream);
 }
 
@@ -961,6 +962,7 @@ int stego_extract_batched(const stego_desc *d_descs, uint32_t n, stego_result *d
                           uint32_t flags, const stego_tune *tune, void *d_ws, uint64_t ws_bytes,
                           void *stream)
 {
+    stego::Trace trace_("stego_extract_batched");
     return batched<false>(d_descs, n, d_results, flags, tune, d_ws, ws_bytes, stream);
 }
 
@@ -968,6 +970,7 @@ int stego_graph_capture_batched(int op, const stego_desc *d_descs, uint32_t n,
                                 stego_result *d_results, uint32_t flags, const stego_tune *tune,
                                 void *d_ws, uint64_t ws_bytes, stego_graph **out)
 {
+    stego::Trace trace_("stego_graph_capture_batched");
     if (!out || (op != STEGO_OP_EMBED_BATCHED && op != STEGO_OP_EXTRACT_BATCHED))
         return STEGO_E_INVAL;
     *out = nullptr;
@@ -1084,6 +1087,7 @@ extern "C" int stego_embed_batched_noalloc(const stego_desc *d_descs, uint32_t n
                                            stego_result *d_results, uint32_t flags,
                                            const stego_tune *tune, void *stream)
 {
+    stego::Trace trace_("stego_embed_batched_noalloc");
     // argument errors first, as stego_embed_batched reports them
     if (flags & ~(uint32_t)STEGO_FUSE_STATS)
         return STEGO_E_INVAL;

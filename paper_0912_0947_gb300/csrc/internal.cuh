@@ -4,10 +4,21 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "stego.h"
 
 namespace stego {
+
+// A named range on the calling host thread for profilers and tracers that
+// attach through NVTX (nothing but a pointer test when none is attached):
+// every entry point, batch and pipeline chunk opens one.
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Launch shapes

@@ -349,6 +349,7 @@ cudaError_t d2h(void *dst, const void *src, uint64_t n, cudaStream_t s)
 int launch_chunk(stego_pipeline *p, uint32_t j, const stego_host_job *jobs, bool embed,
                  uint32_t flags)
 {
+    stego::Trace trace_("stego_pipeline chunk");
     SlotState &sl = p->slot[j];
     char *base = slot_base(p, j);
     uint8_t *data = reinterpret_cast<uint8_t *>(base + p->L.data);
@@ -680,12 +681,14 @@ int stego_pipeline_create(const stego_pipeline_config *cfg, void *d_arena, uint6
 int stego_pipeline_embed(stego_pipeline *p, const stego_host_job *jobs, uint32_t n,
                          stego_result *results, stego_result *readback_results, uint32_t flags)
 {
+    stego::Trace trace_("stego_pipeline_embed");
     return run(p, jobs, n, results, readback_results, flags, true);
 }
 
 int stego_pipeline_extract(stego_pipeline *p, const stego_host_job *jobs, uint32_t n,
                            stego_result *results)
 {
+    stego::Trace trace_("stego_pipeline_extract");
     return run(p, jobs, n, results, nullptr, 0, false);
 }
 

@@ -210,6 +210,7 @@ struct stego_server {
             }
             if (s.members.empty())
                 break; // nothing admissible now
+            stego::Trace trace_("stego_server batch");
             for (const Member &m : s.members) {
                 stego_desc d;
                 std::memset(&d, 0, sizeof(d));
