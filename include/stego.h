@@ -560,8 +560,8 @@ int stego_pipeline_destroy(stego_pipeline *p);
  *   bytes       host array of n cover sizes (the work of each cover).
  *   rank_of     host array of n: the GPU (0..world-1) of each cover.
  *   rank_bytes  optional host array of world: bytes assigned to each GPU.
- * Returns STEGO_OK, or STEGO_E_INVAL for world == 0 or a null array with
- * n > 0. */
+ * Returns STEGO_OK, or STEGO_E_INVAL for world == 0, world > 65536 or a
+ * null array with n > 0. */
 int stego_partition(const uint64_t *bytes, uint32_t n, uint32_t world, uint32_t *rank_of,
                     uint64_t *rank_bytes);
 

@@ -12,28 +12,38 @@
 //
 // Host code only; no CUDA call.
 #include <algorithm>
+#include <functional>
 #include <numeric>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
 
+// More ranks than any machine runs processes for is a caller's mistake.
+constexpr uint32_t kMaxWorld = 1u << 16;
+
 extern "C" int stego_partition(const uint64_t *bytes, uint32_t n, uint32_t world,
                                uint32_t *rank_of, uint64_t *rank_bytes)
 {
-    if (world == 0 || (n > 0 && (!bytes || !rank_of)))
+    if (world == 0 || world > kMaxWorld || (n > 0 && (!bytes || !rank_of)))
         return STEGO_E_INVAL;
     std::vector<uint64_t> load(world, 0);
     std::vector<uint32_t> order(n);
     std::iota(order.begin(), order.end(), 0u);
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return bytes[a] > bytes[b]; });
+    // the least-loaded rank (the lowest of equals) on top of a heap
+    using Entry = std::pair<uint64_t, uint32_t>;
+    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> heap;
+    for (uint32_t r = 0; r < world; ++r)
+        heap.push(Entry(0, r));
     for (uint32_t i : order) {
-        uint32_t r = 0;
-        for (uint32_t k = 1; k < world; ++k)
-            if (load[k] < load[r])
-                r = k;
-        rank_of[i] = r;
-        load[r] += bytes[i];
+        const Entry e = heap.top();
+        heap.pop();
+        rank_of[i] = e.second;
+        load[e.second] = e.first + bytes[i];
+        heap.push(Entry(load[e.second], e.second));
     }
     if (rank_bytes)
         std::copy(load.begin(), load.end(), rank_bytes);

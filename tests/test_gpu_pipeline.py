@@ -241,3 +241,52 @@ def test_pipeline_config_and_argument_errors(S):
     assert e.value.status == S.E_INVAL
     assert pipe.embed(S.Pipeline.jobs([])) == []
     pipe.close()
+
+
+def test_pipeline_edge_cases(S, O):
+    """Empty covers and messages, a batch whose every job is refused, and a
+    job that exactly fills a slot (cover + message + 1280 bytes, staged by
+    its read-back) next to one a byte too large."""
+    rng = np.random.default_rng(7)
+    C, m = 1 << 20, 1000
+    slot = C + m + 1280 + (m + 255) // 256 * 256
+    pipe = S.Pipeline(slots=2, max_descs=4, slot_bytes=slot, mode=S.PIPE_STAGED)
+    cover = rng.integers(0, 256, C + 1, dtype=np.uint8)
+    msg = rng.integers(0, 256, m, dtype=np.uint8)
+    c_fit, c_big = pinned(cover[:C].copy()), pinned(cover.copy())
+    m_h = pinned(msg)
+    o_fit = pinned(np.full(C, 0x5A, np.uint8))
+    o_big = pinned(np.full(C + 1, 0x5A, np.uint8))
+    rb_fit = pinned(np.full(m, 0xEE, np.uint8))
+    rb_big = pinned(np.full(m, 0xEE, np.uint8))
+    empty = pinned(np.zeros(0, np.uint8))
+    recs = [dict(cover=c_fit, stego=o_fit, msg=m_h, readback=rb_fit, cover_bytes=C,
+                 msg_bytes=m, flags=S.HEADER_BE32),
+            dict(cover=c_big, stego=o_big, msg=m_h, readback=rb_big, cover_bytes=C + 1,
+                 msg_bytes=m, flags=S.HEADER_BE32),
+            dict(cover=empty, stego=empty, msg=empty, cover_bytes=0, msg_bytes=0, flags=0),
+            dict(cover=c_fit, stego=o_fit, msg=empty, cover_bytes=C, msg_bytes=0, flags=0)]
+    res, rb = pipe.embed(S.Pipeline.jobs(recs), S.FUSE_STATS, readback_results=True)
+    st, want = O.stream1_embed(cover[:C], msg, header=True)
+    assert res[0]["status"] == 0 and rb[0]["status"] == 0 and rb[0]["msg_bytes"] == m
+    assert res[1]["status"] == S.E_NOMEM and rb[1]["status"] == S.E_NOMEM
+    assert bool((o_big == 0x5A).all()) and bool((rb_big == 0xEE).all())
+    assert res[2]["status"] == 0 and res[2]["msg_bytes"] == 0
+    # the raw empty message leaves the stego equal to the cover
+    assert res[3]["status"] == 0 and np.array_equal(o_fit.numpy(), cover[:C])
+    assert np.array_equal(rb_fit.numpy(), msg)
+    # every job refused: nothing staged, nothing written
+    bad = [dict(cover=c_fit, stego=o_big[:C], msg=m_h, cover_bytes=C, msg_bytes=C, flags=0),
+           dict(cover=c_fit, stego=o_big[:C], msg=m_h, cover_bytes=C, msg_bytes=m, flags=0x4000)]
+    o_big.fill_(0x5A)
+    res = pipe.embed(S.Pipeline.jobs(bad))
+    assert [r["status"] for r in res] == [S.E_CAPACITY, S.E_INVAL]
+    assert bool((o_big == 0x5A).all())
+    # an extraction of an empty-message stego (header 0) writes no byte
+    st0, w0 = O.stream1_embed(cover[:C], np.zeros(0, np.uint8), header=True)
+    s0 = pinned(w0)
+    out0 = pinned(np.full(8, 0xCD, np.uint8))
+    rx = pipe.extract(S.Pipeline.jobs([dict(cover=s0, msg=out0, cover_bytes=C, msg_bytes=8,
+                                            flags=S.HEADER_BE32)]))
+    pipe.close()
+    assert rx[0]["status"] == 0 and rx[0]["msg_bytes"] == 0 and bool((out0 == 0xCD).all())

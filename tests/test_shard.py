@@ -40,9 +40,10 @@ def test_partition_small_cases():
     assert rank_of.size == 0 and rank_bytes.tolist() == [0, 0, 0]
     rank_of, rank_bytes = S.stego_partition([4, 4], 5)  # more ranks than covers
     assert rank_of.tolist() == [0, 1] and rank_bytes.tolist() == [4, 4, 0, 0, 0]
-    with pytest.raises(S.StegoError) as e:
-        S.stego_partition([1, 2], 0)
-    assert e.value.status == S.E_INVAL
+    for world in (0, (1 << 16) + 1):
+        with pytest.raises(S.StegoError) as e:
+            S.stego_partition([1, 2], world)
+        assert e.value.status == S.E_INVAL
 
 
 def _batch():
