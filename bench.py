@@ -959,7 +959,7 @@ def run_paper2_leg(S, AT, torch, dev, synth):
 
 def run_streamk_leg(S, AT, torch, dev, synth):
     """The stream layout with k bits per carrying byte on the 8192x8192x3
-    cover at full capacity: k = 2 and 4 over all bytes (algorithmic bytes
+    cover at full capacity: k = 2, 3 and 4 over all bytes (algorithmic bytes
     2C + 8|S|/8 embed, C + |S| extract) and k = 2 on plane 0 (carrying bytes
     every third byte: sectors of the whole cover move)."""
     C = 8192 * 8192 * 3
@@ -969,7 +969,7 @@ def run_streamk_leg(S, AT, torch, dev, synth):
     flush = AT.Flusher(dev)
     peak, _ = hbm_peak()
     out = {}
-    for name, k, geom in (("k2_all", 2, None), ("k4_all", 4, None),
+    for name, k, geom in (("k2_all", 2, None), ("k3_all", 3, None), ("k4_all", 4, None),
                           ("k2_plane0", 2, (8192, 8192, 3, 0))):
         flags = S.BITS(k) | S.HEADER_BE32 | (S.PLANE_ONLY if geom else 0)
         m = S.stego_capacity(C, flags, geom=geom)
@@ -1229,7 +1229,23 @@ def run_misaligned_leg(S, AT, torch, dev, synth):
 
 def run_profile_case(S, torch, dev, synth, spec):
     """--profile-case co,so,mo: one warm-up and one more embed + extract of
-    the misaligned case (for a profiler); prints nothing but a check."""
+    the misaligned case; --profile-case kK: the same with k bits over every
+    byte of the aligned cover at full capacity (for a profiler)."""
+    if spec.startswith("k"):
+        k = int(spec[1:])
+        w = synth.single_8192()
+        cover = w.cover(dev)
+        flags = S.BITS(k) | S.HEADER_BE32
+        m = S.stego_capacity(cover.numel(), flags)
+        msg = synth.uniform_bytes(m, synth.substream(synth.SEED_BASE + 7, 10 + k), dev)
+        stego, got = torch.empty_like(cover), torch.empty_like(msg)
+        res = S.new_result(dev)
+        for _ in range(2):
+            S.stego_embed(cover, stego, msg, flags | S.FUSE_STATS, res)
+            S.stego_extract(stego, got, 0, flags, res)
+        torch.cuda.synchronize(dev)
+        assert torch.equal(got, msg)
+        return {"profile_case": spec, "ok": True}
     co, so, mo = (int(x) for x in spec.split(","))
     w = synth.single_8192()
     bufs, cv, sv, mv, ov, Cm, mm = misaligned_views(S, torch, dev, w, co, so, mo)

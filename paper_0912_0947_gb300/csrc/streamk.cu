@@ -380,7 +380,7 @@ __host__ __device__ constexpr int units_per_iter()
 // Carrying bytes after the last whole unit (fewer than 16) are done by
 // block 0 byte by byte.
 template <int K, int CH, int PLANE, bool STATS>
-__global__ void __launch_bounds__(512) embedk_units(KView a)
+__global__ void __launch_bounds__(512, K >= 3 ? 3 : 0) embedk_units(KView a)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
     allow_dependents();
