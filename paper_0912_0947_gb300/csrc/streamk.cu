@@ -339,17 +339,6 @@ __device__ __forceinline__ uint64_t unit_window(const uint32_t (&g)[4])
         const uint32_t hi = __byte_perm(b[0], b[1], 0x0246u); // b0.l0 b0.l2 b1.l0 b1.l2, first on top
         const uint32_t lo = __byte_perm(b[2], b[3], 0x0246u);
         return ((uint64_t)hi << 32) | lo;
-    } else if constexpr (K == 3) {
-        // 12 bits per word, the four words' bits placed from the top
-        uint64_t X = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t w = g[i];
-            const uint32_t t = ((w & 7u) << 9) | (((w >> 8) & 7u) << 6) |
-                               (((w >> 16) & 7u) << 3) | ((w >> 24) & 7u);
-            X |= (uint64_t)t << (52 - 12 * i);
-        }
-        return X;
     } else {
         constexpr uint32_t MASK = (1u << K) - 1u;
         uint64_t X = 0;
@@ -358,6 +347,24 @@ __device__ __forceinline__ uint64_t unit_window(const uint32_t (&g)[4])
             X |= (uint64_t)((g[t >> 2] >> (8 * (t & 3))) & MASK) << (64 - K * (t + 1));
         return X;
     }
+}
+
+// k = 3: the unit's 48 stream bits as two 24-bit halves (words 0-1, 2-3),
+// first bit on top.  Per word, one multiply by 2^11 + 1 joins the fields of
+// bytes 0, 1 into bits 8-13 and those of bytes 2, 3 into bits 24-29 (the
+// shifted copies do not overlap, so nothing carries); the high half of a
+// second product, by 2^30 + 2^8, puts the first pair above the second at
+// bits 0-11, with a copy of the second pair at bits 22-27 that the 12-bit
+// shift of the first word pushes out and a mask of the second word drops.
+// The multiplies run on the FMA pipe, which the k = 3 gather left idle.
+__device__ __forceinline__ void unit_window3(const uint32_t (&g)[4], uint32_t &v01, uint32_t &v23)
+{
+    uint32_t t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        t[i] = __umulhi(((g[i] & 0x07070707u) * 0x801u) & 0x3F003F00u, 0x40000100u);
+    v01 = (t[0] << 12) | (t[1] & 0xFFFu);
+    v23 = (t[2] << 12) | (t[3] & 0xFFFu);
 }
 
 // Units each thread keeps in flight per loop iteration.  A plane unit is
@@ -661,6 +668,74 @@ __device__ __forceinline__ int extractk_prologue(const KView &a, uint64_t &len)
     return status;
 }
 
+// k = 3 units of the extract: unit u yields the 6 stream bytes [6u, 6u + 6),
+// so a lane pair (units 2j, 2j + 1) holds 12 consecutive message bytes and
+// writes them as three aligned words: the even lane its first four bytes
+// and its last two joined to the odd lane's first two (one shuffle), the
+// odd lane its last four.  The loop runs while the warp's first unit is in
+// range, so every lane reaches the shuffle; pairs at the header, at the
+// message's end or on an unaligned output store 16-bit halves or bytes.
+template <int CH, int PLANE>
+__device__ __forceinline__ void extract3_units(const KView &a, uint64_t nunits, uint64_t hb,
+                                               uint64_t sbytes)
+{
+    constexpr int U = units_per_iter<CH, false>();
+    const uint32_t lane = threadIdx.x & 31u;
+    const bool odd = (lane & 1u) != 0;
+    // stream byte 12j lands at out + 12j - hb: word-aligned for every j or none
+    const bool words = (((uintptr_t)a.out - hb) & 3u) == 0;
+    for (uint64_t u0 = (uint64_t)blockIdx.x * blockDim.x * U + threadIdx.x; u0 - lane < nunits;
+         u0 += (uint64_t)gridDim.x * blockDim.x * U) {
+        uint32_t w[U][4 * CH];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            if (u < nunits) {
+                load_unit<CH>(a.cover, u, w[r]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4 * CH; ++j)
+                    w[r][j] = 0;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const uint64_t u = u0 + (uint64_t)r * blockDim.x;
+            uint32_t g[4], v01, v23;
+            gather_unit<CH, PLANE>(w[r], g);
+            unit_window3(g, v01, v23);
+            const uint32_t P = __byte_perm(v01, v23, 0x6012u); // stream bytes 0-3, memory order
+            const uint32_t Q = __byte_perm(v23, 0u, 0x4401u);  // stream bytes 4-5
+            const uint32_t Pn = __shfl_down_sync(0xFFFFFFFFu, P, 1);
+            const uint64_t q2 = 6u * (u & ~1ull); // first stream byte of the pair
+            if (words && (u | 1u) < nunits && q2 >= hb && q2 + 12 <= sbytes) {
+                uint32_t *op = reinterpret_cast<uint32_t *>(a.out + (q2 - hb));
+                if (odd) {
+                    op[2] = __byte_perm(P, Q, 0x5432u);
+                } else {
+                    op[0] = P;
+                    op[1] = __byte_perm(Q, Pn, 0x5410u);
+                }
+            } else if (u < nunits) {
+                const uint64_t q0 = 6u * u; // first stream byte of the unit
+                if (q0 >= hb && q0 + 6 <= sbytes && ((q0 - hb + (uintptr_t)a.out) & 1u) == 0) {
+                    unsigned short *op = reinterpret_cast<unsigned short *>(a.out + (q0 - hb));
+                    op[0] = (unsigned short)P;
+                    op[1] = (unsigned short)(P >> 16);
+                    op[2] = (unsigned short)Q;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const uint64_t q = q0 + i;
+                        if (q >= hb && q < sbytes)
+                            a.out[q - hb] = (uint8_t)(i < 3 ? v01 >> (16 - 8 * i) : v23 >> (40 - 8 * i));
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Extract over units (stego 16-byte aligned): unit u yields stream bytes
 // [2Ku, 2Ku + 2K); U units per thread per iteration, loads first.  Stream
 // bytes past the last whole unit go bit by bit.
@@ -685,6 +760,10 @@ __global__ void __launch_bounds__(512) extractk_units(KView a)
         for (int i = 0; i < 8; ++i)
             v |= stream_bit(a, 8u * q + i) << (7 - i);
         a.out[q - hb] = (uint8_t)v;
+    }
+    if constexpr (K == 3) {
+        extract3_units<CH, PLANE>(a, nunits, hb, sbytes);
+        return;
     }
     constexpr int U = units_per_iter<CH, false>();
     for (uint64_t u0 = (uint64_t)blockIdx.x * blockDim.x * U + threadIdx.x; u0 < nunits;
@@ -713,12 +792,6 @@ __global__ void __launch_bounds__(512) extractk_units(KView a)
                 for (int i = 0; i < K / 2; ++i)
                     reinterpret_cast<uint32_t *>(op)[i] =
                         __byte_perm((uint32_t)(X >> (32 - 32 * i)), 0u, 0x0123u);
-            } else if (K == 3 && q0 >= hb && q0 + 6 <= sbytes && (((uintptr_t)op & 1u) == 0)) {
-                // three 16-bit stores (2-byte aligned message bytes)
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    reinterpret_cast<unsigned short *>(op)[i] = (unsigned short)__byte_perm(
-                        (uint32_t)(X >> (48 - 16 * i)) & 0xFFFFu, 0u, 0x4401u);
             } else {
 #pragma unroll
                 for (int i = 0; i < 2 * K; ++i) {

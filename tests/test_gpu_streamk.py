@@ -85,6 +85,33 @@ def test_all_bytes(S, O, k, C):
     _check(S, O, cover, msg, k, True, offs=(3, 7, 1))
 
 
+@pytest.mark.parametrize("out_off", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("header", [True, False])
+def test_extract_k3_output_alignment(S, O, out_off, header):
+    """k = 3 extraction from an aligned stego into outputs at every offset
+    mod 4 (word stores by lane pairs, 16-bit halves, bytes), with message
+    ends at every position of a 12-byte lane pair and several grid-stride
+    rounds."""
+    C = 3 * 65536 + 48 + 5   # 12291 units and a ragged tail
+    rng = np.random.default_rng(31 + out_off + 8 * header)
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    flags = S.BITS(3) | (S.HEADER_BE32 if header else 0)
+    cap = S.stego_capacity(C, flags)
+    for m in sorted({0, 1, 2, 7, 8, 13, cap // 2 + 3} | {cap - d for d in range(13)}):
+        msg = rng.integers(0, 256, m, dtype=np.uint8)
+        st, stego = O.streamk_embed(cover, msg, 3, header=header)
+        assert st == oracle.OK
+        gst = Guarded(C, 0, stego)
+        gx = Guarded(m + 5, out_off, 0xEE)
+        res = S.new_result()
+        S.stego_extract(gst.view, gx.view, m, flags, res)
+        r = S.read_result(res)
+        assert r["status"] == 0 and r["msg_bytes"] == m
+        out = gx.host()
+        assert np.array_equal(out[:m], msg), (m, out_off, header)
+        assert np.all(out[m:] == 0xEE) and gx.canaries_intact()
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("geom", [(4, 1, 3, 1), (17, 5, 3, 0), (64, 9, 4, 3), (100, 7, 1, 0),
                                   (33, 33, 2, 1)])
@@ -124,7 +151,7 @@ def test_errors(S):
     assert S.read_result(res)["status"] == S.E_BAD_HEADER
 
 
-@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("k", [2, 3, 4])
 def test_full_size_8192(S, O, k):
     """The 8192x8192x3 cover at full k-bit capacity, every byte against the
     oracle."""
