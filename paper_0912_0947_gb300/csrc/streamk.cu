@@ -173,7 +173,9 @@ __device__ __noinline__ uint4 stream_end_vector(const KView &a, uint64_t v, uint
 
 // Stream bytes [2Kv, 2Kv + 2K) as a big-endian 64-bit word (whole vector
 // inside the stream): word loads when they are message bytes on a 4-byte
-// boundary, byte loads otherwise.
+// boundary, byte loads otherwise.  K = 3 packs its 6 bytes as two 24-bit
+// halves instead, bytes 0-2 in the high word and 3-5 in the low one, each
+// first byte on top (the form unit_fields<3> spreads).
 template <int K>
 __device__ __forceinline__ uint64_t stream_window(const KView &a, uint64_t v)
 {
@@ -183,17 +185,23 @@ __device__ __forceinline__ uint64_t stream_window(const KView &a, uint64_t v)
     const uint8_t *mp = a.msg + (q0 - hb);
     // q0 is a multiple of 4 for even K (of 2 for K = 3), so mp's alignment
     // is the launch's
-    if ((K & 1) == 0 && q0 >= hb && a.msg_w4) {
+    if constexpr (K == 3) {
+        uint32_t v01, v23;
+        if (q0 >= hb && a.msg_w2) {
+            const unsigned short *hp = reinterpret_cast<const unsigned short *>(mp);
+            const uint32_t h0 = __ldg(hp), h1 = __ldg(hp + 1), h2 = __ldg(hp + 2);
+            v01 = __byte_perm(h0, h1, 0x2014u); // bytes 0, 1, 2 from the top; byte 3 zero
+            v23 = __byte_perm(h1, h2, 0x2145u); // bytes 3, 4, 5
+        } else {
+            v01 = (sbyte(a, q0) << 16) | (sbyte(a, q0 + 1) << 8) | sbyte(a, q0 + 2);
+            v23 = (sbyte(a, q0 + 3) << 16) | (sbyte(a, q0 + 4) << 8) | sbyte(a, q0 + 5);
+        }
+        return ((uint64_t)v01 << 32) | v23;
+    } else if ((K & 1) == 0 && q0 >= hb && a.msg_w4) {
 #pragma unroll
         for (int i = 0; i < K / 2; ++i) {
             const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(mp) + i);
             X |= (uint64_t)__byte_perm(w, 0u, 0x0123u) << (32 - 32 * i);
-        }
-    } else if (K == 3 && q0 >= hb && a.msg_w2) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const uint32_t h = __ldg(reinterpret_cast<const unsigned short *>(mp) + i);
-            X |= (uint64_t)__byte_perm(h, 0u, 0x4401u) << (48 - 16 * i); // bytes swapped
         }
     } else {
 #pragma unroll
@@ -275,9 +283,12 @@ __device__ __forceinline__ void scatter_xor(uint32_t (&w)[4 * CH], const uint32_
 
 // Word i (carrying bytes 4i..4i+3, field in each byte's low K bits) of a
 // unit whose stream window is X (stream bytes big-endian, the first in bits
-// 56..63).  K = 1, 4 fill the four byte lanes from replicated stream bytes
-// with fixed per-lane shifts, K = 2 with one multiply; K = 3 (fields across
-// byte boundaries) takes each word's 12 bits and cuts them field by field.
+// 56..63; for K = 3 two 24-bit halves).  K = 1, 4 fill the four byte lanes
+// from replicated stream bytes with fixed per-lane shifts, K = 2 with one
+// multiply; K = 3 (fields across byte boundaries) takes the word's 12 bits
+// t and multiplies by 2^24 + 4: the two copies of t do not overlap, and
+// leave fields 1, 3 at bits 8, 24 and fields 0, 2 at bits 11, 27, which one
+// shift by 11 brings to bits 0, 16.
 template <int K>
 __device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
 {
@@ -297,10 +308,10 @@ __device__ __forceinline__ uint32_t unit_fields(uint64_t X, int i)
         const uint32_t r = __byte_perm(i < 2 ? hi : lo, 0u, (i & 1) ? 0x0011u : 0x2233u);
         return ((r >> 4) & 0x000F000Fu) | (r & 0x0F000F00u);
     } else if constexpr (K == 3) {
-        // the word's 12 bits, then one 3-bit field per lane
-        const uint32_t t = (uint32_t)(X >> (52 - 12 * i)) & 0xFFFu;
-        return ((t >> 9) & 7u) | (((t >> 6) & 7u) << 8) | (((t >> 3) & 7u) << 16) |
-               ((t & 7u) << 24);
+        const uint32_t h = i < 2 ? hi : lo;
+        const uint32_t t = (i & 1) ? (h & 0xFFFu) : (h >> 12);
+        const uint32_t p = t * 0x01000004u;
+        return (p & 0x07000700u) | ((p & 0x38003800u) >> 11);
     } else {
         constexpr uint32_t MASK = (1u << K) - 1u;
         uint32_t f = 0;
