@@ -289,6 +289,12 @@ def run_ours(args, rank, world, local_rank):
         if sharded:
             legs["batched_uneven_sharded"] = sharded
         torch.cuda.empty_cache()
+    if world > 1 or not args.legs or "split_cover" in args.legs.split(","):
+        # every rank takes part: the one cover split at 16-byte offsets
+        split = run_split_leg(S, AT, torch, dev, stream, rank, world, cover, stego, msg, C, m)
+        if split:
+            legs["split_cover"] = split
+        torch.cuda.empty_cache()
     want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
                                                          "batched_video_paper2", "paper2",
                                                          "streamk", "serving", "small",
@@ -748,9 +754,9 @@ def run_sharded_leg(S, AT, torch, dev, stream, synth, rank, world, count=None):
     def timed(fn, reps=5):
         ts = []
         for _ in range(reps):
-            flush()
             torch.cuda.synchronize(dev)
             dist.barrier()
+            flush()  # ends in a short GPU spin: the call is queued before e0 runs
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
@@ -789,6 +795,76 @@ def run_sharded_leg(S, AT, torch, dev, stream, synth, rank, world, count=None):
             "extract_cover_gbs": round(total / (t_x * 1e-3) / 1e9, 1),
             "scaling": "strong (the same 4096 covers split among the GPUs)",
             "gathered_changed": int(sum(g[1] for g in gathered))}
+
+
+def run_split_leg(S, AT, torch, dev, stream, rank, world, cover, stego, msg, C, m):
+    """The 8192x8192x3 cover at full capacity split among the ranks at
+    16-byte cover offsets (shard.cover_slices): every rank embeds (fused
+    statistics) and extracts only its own slice, reading the header from
+    the first 32 stego bytes like a rank without the message length would.
+    With one process the slice is the whole cover (the split's own cost:
+    the header's four bytes go through a call of their own).  Each timed
+    call starts after a barrier; the time is the slowest rank's."""
+    from paper_0912_0947_gb300 import shard
+    c0, c1 = shard.cover_slices(C, world)[rank]
+    lo, hi = shard.slice_message_range(c0, c1, m)
+    cs, part = cover[c0:c1], msg[lo:hi]
+    st = torch.empty(c1 - c0, dtype=torch.uint8, device=dev)
+    out = torch.empty(max(hi - lo, 1), dtype=torch.uint8, device=dev)
+    head = stego[:32]  # rank 0's first stego bytes, written by the single-cover embed
+    flush = AT.Flusher(dev)
+
+    mm = shard.read_header(head, C, stream=stream)
+    emb_sl = shard.CoverSlice(c0, c1, C, m, device=dev)
+    ext_sl = shard.CoverSlice(c0, c1, C, mm, device=dev)
+
+    def emb():
+        emb_sl.embed(cs, st, part, stream=stream)
+
+    def ext():
+        ext_sl.extract(st, out, stream=stream)
+
+    def timed(fn, reps=9):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            flush()  # ends in a short GPU spin: the calls are queued before e0 runs
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(max_over_ranks(e0.elapsed_time(e1), world, dev))
+        return sorted(ts)[len(ts) // 2]
+
+    emb()
+    ext()
+    torch.cuda.synchronize(dev)
+    ok = (mm == m and torch.equal(st, stego[c0:c1]) and torch.equal(out[: hi - lo], part))
+    ch, ss = emb_sl.stats(stream)
+    t_e = timed(emb)
+    t_x = timed(ext)
+    oks = [ok]
+    if world > 1:
+        import torch.distributed as dist
+        oks = [None] * world
+        dist.all_gather_object(oks, (ok, ch))
+        oks = [o[0] for o in oks]
+    if rank != 0:
+        return None
+    assert all(oks), "split cover differs from the single-cover embed"
+    return {"workload": "8192x8192x3 cover (201,326,592 B) at full one-bit capacity split among "
+                        "%d GPUs at 16-byte cover offsets, one slice per GPU" % world,
+            "ranks": world, "slice_bytes": [b - a for a, b in shard.cover_slices(C, world)],
+            "embed_ms_slowest_rank": round(t_e, 4), "extract_ms_slowest_rank": round(t_x, 4),
+            "embed_cover_gbs": round(C / (t_e * 1e-3) / 1e9, 1),
+            "extract_cover_gbs": round(C / (t_x * 1e-3) / 1e9, 1),
+            "header_read": "once per cover before the timed extractions: the header's 4 "
+                           "bytes extracted from the first 32 stego bytes and read back",
+            "scaling": "strong (one cover split among the GPUs)"}
 
 
 # launch shape of the server's batched calls: the library's built-in
@@ -1667,7 +1743,8 @@ def main():
     ap.add_argument("--legs", default="",
                     help="comma list of extra legs: batched_uneven,batched_video,"
                          "batched_video_paper2,paper2,streamk,serving,small,extract_gather,"
-                         "batched_uneven_host,batched_uneven_misaligned,single_misaligned, "
+                         "batched_uneven_host,batched_uneven_misaligned,single_misaligned,"
+                         "split_cover, "
                          "or none "
                          "(default all)")
     args = ap.parse_args()

@@ -105,3 +105,111 @@ def test_sharded_two_gloo_ranks_equal_one_process(tmp_path):
     assert abs(b[0] - b[1]) <= max(sizes)
     # one process, no collective: the same results
     assert shard.run_sharded(sizes, 0, 1, _compute) == want
+
+
+# ---------------------------------------------------------------- one cover
+
+def test_cover_slices_tile_the_cover():
+    for C in (0, 5, 16, 100, 4097, (1 << 20) + 3):
+        for world in range(1, 10):
+            sl = shard.cover_slices(C, world)
+            assert len(sl) == world and sl[0][0] == 0 and sl[-1][1] == C
+            assert all(a % 16 == 0 and a <= b for a, b in sl)
+            assert all(sl[i][1] == sl[i + 1][0] for i in range(world - 1))
+            sizes = [b - a for a, b in sl]
+            assert max(sizes) - min(sizes) <= 16 + 15
+    with pytest.raises(ValueError):
+        shard.cover_slices(10, 0)
+
+
+@pytest.mark.parametrize("header", [True, False])
+def test_slice_message_ranges_partition_the_message(header):
+    for C in (32, 48, 1000, 4097, 65536 + 40):
+        cap = S.stego_capacity(C, S.HEADER_BE32 if header else 0)
+        for m in sorted({0, min(1, cap), cap // 2, cap}):
+            for world in (1, 2, 3, 7):
+                got = []
+                for c0, c1 in shard.cover_slices(C, world):
+                    for kind, a, b, lo, hi in shard.slice_pieces(c0, c1, m, header):
+                        assert c0 <= a < b <= c1 and a % 8 == 0
+                        if kind == "msg":
+                            got.append((lo, hi))
+                            assert 8 * (lo + (4 if header else 0)) == a or lo == hi
+                        else:
+                            assert header and b <= 32 and (lo, hi) == (a // 8, b // 8)
+                lo_hi = [r for r in got if r[1] > r[0]]
+                assert all(lo_hi[i][1] == lo_hi[i + 1][0] for i in range(len(lo_hi) - 1))
+                if m:
+                    assert (lo_hi[0][0], lo_hi[-1][1]) == (0, m)
+                else:
+                    assert lo_hi == []
+
+
+def _oracle_slice(O, cover, msg, c0, c1, m, header):
+    """One slice through its pieces, each a raw oracle embed."""
+    parts, ch, ss = [], 0, 0
+    for kind, a, b, lo, hi in shard.slice_pieces(c0, c1, m, header):
+        src = (np.frombuffer(shard.header_bytes(m), np.uint8)[lo:hi] if kind == "header"
+               else msg[lo:hi])
+        st, w = O.stream1_embed(cover[a:b], src, header=False)
+        assert st == 0
+        parts.append(w)
+        c, s_ = O.changed_bytes(cover[a:b], w)
+        ch, ss = ch + c, ss + s_
+    return (np.concatenate(parts) if parts else np.zeros(0, np.uint8)), ch, ss
+
+
+@pytest.mark.parametrize("header", [True, False])
+def test_slices_through_raw_pieces_equal_one_embed(header):
+    """The slice plan executed with the oracle's raw embed reproduces the
+    oracle's embed of the whole stream, stats included."""
+    import oracle
+    O = oracle.load()
+    rng = np.random.default_rng(77 + header)
+    for C in (32, 40, 1000, 4101, 3 * 4096 + 16 + 7):
+        cover = rng.integers(0, 256, C, dtype=np.uint8)
+        cap = S.stego_capacity(C, S.HEADER_BE32 if header else 0)
+        for m in sorted({0, min(1, cap), cap // 3, cap}):
+            msg = rng.integers(0, 256, m, dtype=np.uint8)
+            st, want = O.stream1_embed(cover, msg, header=header)
+            assert st == 0
+            for world in (1, 2, 3, 5, 8):
+                got, ch, ss = [], 0, 0
+                for c0, c1 in shard.cover_slices(C, world):
+                    w, c, s_ = _oracle_slice(O, cover, msg, c0, c1, m, header)
+                    assert w.size == c1 - c0
+                    got.append(w)
+                    ch, ss = ch + c, ss + s_
+                assert np.array_equal(np.concatenate(got), want), (C, m, world)
+                assert (ch, ss) == O.changed_bytes(cover, want)
+
+
+def _split_rank(rank, world, port, path):
+    import torch.distributed as dist
+    import oracle
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    O = oracle.load()
+    rng = np.random.default_rng(123)
+    C = 20000 + 7
+    cover = rng.integers(0, 256, C, dtype=np.uint8)
+    m = S.stego_capacity(C, S.HEADER_BE32) - 5
+    msg = rng.integers(0, 256, m, dtype=np.uint8)
+    c0, c1 = shard.cover_slices(C, world)[rank]
+    w, ch, ss = _oracle_slice(O, cover, msg, c0, c1, m, True)
+    got = shard.gather_results(np.array([rank]), [(w.tobytes(), ch, ss)], world)
+    if rank == 0:
+        st, want = O.stream1_embed(cover, msg, header=True)
+        ok = (b"".join(g[0] for g in got) == want.tobytes() and
+              (sum(g[1] for g in got), sum(g[2] for g in got)) == O.changed_bytes(cover, want))
+        with open(path, "w") as f:
+            json.dump({"ok": bool(ok), "ranks": len(got)}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_single_cover_split_two_gloo_ranks(tmp_path):
+    path = str(tmp_path / "split.json")
+    mp.spawn(_split_rank, args=(2, _free_port(), path), nprocs=2, join=True)
+    with open(path) as f:
+        assert json.load(f) == {"ok": True, "ranks": 2}
