@@ -295,13 +295,13 @@ def run_ours(args, rank, world, local_rank):
         if split:
             legs["split_cover"] = split
         torch.cuda.empty_cache()
-    want = set(args.legs.split(",")) if args.legs else {"batched_uneven", "batched_video",
-                                                         "batched_video_paper2", "paper2",
-                                                         "streamk", "serving", "small",
-                                                         "extract_gather",
-                                                         "batched_uneven_host",
-                                                         "batched_uneven_misaligned",
-                                                         "single_misaligned"}
+    single_gpu_legs = {"batched_uneven", "batched_video", "batched_video_paper2", "paper2",
+                       "streamk", "serving", "small", "extract_gather", "batched_uneven_host",
+                       "batched_uneven_misaligned", "single_misaligned"}
+    # with several GPUs the run is the replicated step and the two splits
+    # above; the one-GPU legs are the N = 1 run's (the other GPUs would idle
+    # while rank 0 repeated them)
+    want = set(args.legs.split(",")) if args.legs else (single_gpu_legs if world == 1 else set())
     if args.no_batched:
         want -= {"batched_uneven", "batched_video", "batched_video_paper2", "paper2", "streamk",
                  "batched_uneven_host", "batched_uneven_misaligned"}
@@ -1746,7 +1746,7 @@ def main():
                          "batched_uneven_host,batched_uneven_misaligned,single_misaligned,"
                          "split_cover, "
                          "or none "
-                         "(default all)")
+                         "(default: all with one GPU, none with several)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
