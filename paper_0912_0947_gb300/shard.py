@@ -145,7 +145,10 @@ class CoverSlice:
             raise ValueError("slice tensors must hold %d bytes" % n)
         if (0 if msg_part is None else msg_part.numel()) != self.hi - self.lo:
             raise ValueError("msg_part must hold message bytes [%d, %d)" % (self.lo, self.hi))
-        for i, (kind, a, b, plo, phi) in enumerate(self.pieces):
+        # the pieces write disjoint bytes: the message piece goes first, so
+        # the header's small launch waits on it instead of delaying it
+        for i in reversed(range(len(self.pieces))):
+            kind, a, b, plo, phi = self.pieces[i]
             src = self.hdr if kind == "header" else (msg_part if phi > plo else None)
             stego_embed(cover_s[a - self.c0: b - self.c0], stego_s[a - self.c0: b - self.c0],
                         src, FUSE_STATS, self.results[i], stream=stream)
