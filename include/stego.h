@@ -346,7 +346,11 @@ int stego_graph_destroy(stego_graph *g);
  * the sum of their working-set bytes (embed: 2*cover_bytes + msg_bytes;
  * extract: cover_bytes + msg_bytes) stays within budget_bytes, up to
  * max_batch requests, and launches them as one stego_embed_batched plus one
- * stego_extract_batched on that slot's stream.  Requests arriving while
+ * stego_extract_batched on that slot's stream; the batch's stream-layout
+ * requests with STEGO_BITS(k), k > 1, or STEGO_PLANE_ONLY (which the
+ * batched kernels do not take) follow as stego_embed / stego_extract calls
+ * on the same stream, a request they refuse completing with that status.
+ * Requests arriving while
  * batches run are admitted into the next free slot as soon as budget frees
  * up, so batches overlap on the device.  A request whose own bytes exceed
  * the budget completes at once with STEGO_E_NOMEM; an unknown op with
@@ -366,10 +370,11 @@ typedef struct stego_server_config {
 
 typedef struct stego_request {
     uint32_t op;           /* STEGO_OP_EMBED or STEGO_OP_EXTRACT            */
-    uint32_t flags;        /* as stego_desc.flags: STEGO_LAYOUT_STREAM1     */
-                           /* [| STEGO_HEADER_BE32] or STEGO_LAYOUT_PAPER2  */
-                           /* (with geom); k-bit and one-plane stream       */
-                           /* requests complete with STEGO_E_INVAL          */
+    uint32_t flags;        /* STEGO_LAYOUT_STREAM1 [| STEGO_HEADER_BE32]    */
+                           /* [| STEGO_BITS(k)] [| STEGO_PLANE_ONLY, with   */
+                           /* geom] or STEGO_LAYOUT_PAPER2 (with geom);     */
+                           /* k > 1 and one-plane requests run as single-   */
+                           /* cover calls inside their batch                */
     const uint8_t *cover;  /* embed: cover; extract: stego image            */
     uint8_t *stego;        /* embed: output image                           */
     uint8_t *msg;          /* embed: message (read); extract: output buffer */
@@ -377,7 +382,7 @@ typedef struct stego_request {
     uint64_t msg_bytes;    /* embed: length; extract: capacity of msg       */
     uint64_t msg_len;      /* extract without a header: bytes to extract    */
     uint64_t tag;          /* returned in the completion                    */
-    stego_geom geom;       /* STEGO_LAYOUT_PAPER2 geometry                  */
+    stego_geom geom;       /* PAPER2 / STEGO_PLANE_ONLY geometry            */
 } stego_request;           /* 80 bytes */
 
 typedef struct stego_completion {

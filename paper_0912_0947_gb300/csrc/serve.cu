@@ -10,6 +10,10 @@
 //     while their working-set bytes fit the budget, up to max_batch per
 //     batch, and launches them as one batched embed and/or one batched
 //     extract on that slot's stream.
+// Stream-layout requests with k > 1 bits per byte or one carrying plane
+// (which the batched kernels do not take) ride in the same batch as calls
+// of their own to the single-cover entry points on the slot's stream; their
+// results sit after the batched ones in the slot's result arrays.
 // Requests that arrive while batches run are admitted into the next free
 // slot as soon as the budget allows, so batches overlap on the device.  A
 // request larger than the whole budget completes at once with
@@ -47,9 +51,17 @@ struct Pending {
 struct Member {
     Pending p;
     bool embed;
+    bool single;    // served by a single-cover call instead of the batched one
     uint32_t index; // into the slot's embed or extract arrays
     double t_dispatch;
 };
+
+// k > 1 bits per byte or one carrying plane in the stream layout.
+bool single_cover_only(uint32_t flags)
+{
+    return (flags & STEGO_LAYOUT_MASK) == STEGO_LAYOUT_STREAM1 &&
+           (flags & (STEGO_BITS_MASK | STEGO_PLANE_ONLY)) != 0;
+}
 
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -170,6 +182,31 @@ struct stego_server {
         return any;
     }
 
+    // The slot's single-cover members of one direction, each a call of its
+    // own on the slot's stream writing its result entry.  A request the call
+    // refuses on the host gets that status in its result, as the batched
+    // prep reports refused descriptors; only a CUDA failure fails the batch.
+    int launch_singles(Slot &s, bool embed)
+    {
+        for (const Member &m : s.members) {
+            if (!m.single || m.embed != embed)
+                continue;
+            const stego_request &r = m.p.req;
+            const stego_geom *g = (r.flags & STEGO_PLANE_ONLY) ? &r.geom : nullptr;
+            stego_result *res = (embed ? s.d_res_e : s.d_res_x) + m.index;
+            const int st = embed ? stego_embed(r.cover, r.stego, r.cover_bytes, r.msg,
+                                               r.msg_bytes, g, r.flags | STEGO_FUSE_STATS, res,
+                                               s.stream)
+                                 : stego_extract(r.cover, r.cover_bytes, r.msg, r.msg_bytes,
+                                                 r.msg_len, g, r.flags, res, s.stream);
+            if (st == STEGO_E_CUDA)
+                return st;
+            if (st != STEGO_OK && stego::write_result(res, 0, st, s.stream) != cudaSuccess)
+                return STEGO_E_CUDA;
+        }
+        return STEGO_OK;
+    }
+
     // Admit queued requests into a free slot and launch them.
     bool dispatch()
     {
@@ -198,6 +235,7 @@ struct stego_server {
                     Member m;
                     m.p = p;
                     m.embed = p.req.op == STEGO_OP_EMBED;
+                    m.single = single_cover_only(p.req.flags);
                     m.index = m.embed ? ne++ : nx++;
                     m.t_dispatch = t;
                     in_flight_bytes += p.bytes;
@@ -211,7 +249,21 @@ struct stego_server {
             if (s.members.empty())
                 break; // nothing admissible now
             stego::Trace trace_("stego_server batch");
+            // batched members first (descriptors 0..nbe-1 / 0..nbx-1), the
+            // single-cover ones after them
+            uint32_t nbe = 0, nbx = 0;
+            for (Member &m : s.members)
+                if (!m.single)
+                    m.index = m.embed ? nbe++ : nbx++;
+            {
+                uint32_t ie = nbe, ix = nbx;
+                for (Member &m : s.members)
+                    if (m.single)
+                        m.index = m.embed ? ie++ : ix++;
+            }
             for (const Member &m : s.members) {
+                if (m.single)
+                    continue;
                 stego_desc d;
                 std::memset(&d, 0, sizeof(d));
                 d.cover = m.p.req.cover;
@@ -226,24 +278,28 @@ struct stego_server {
             }
             int st = STEGO_OK;
             if (ne) {
-                if (cudaMemcpyAsync(s.d_desc_e, s.h_desc_e, sizeof(stego_desc) * ne,
-                                    cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
+                if (nbe && cudaMemcpyAsync(s.d_desc_e, s.h_desc_e, sizeof(stego_desc) * nbe,
+                                           cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
                     st = STEGO_E_CUDA;
-                if (st == STEGO_OK)
-                    st = stego_embed_batched(s.d_desc_e, ne, s.d_res_e, STEGO_FUSE_STATS,
+                if (st == STEGO_OK && nbe)
+                    st = stego_embed_batched(s.d_desc_e, nbe, s.d_res_e, STEGO_FUSE_STATS,
                                              &cfg.tune_embed, s.d_ws_e, s.ws_bytes, s.stream);
+                if (st == STEGO_OK && ne > nbe)
+                    st = launch_singles(s, true);
                 if (st == STEGO_OK &&
                     cudaMemcpyAsync(s.h_res_e, s.d_res_e, sizeof(stego_result) * ne,
                                     cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
                     st = STEGO_E_CUDA;
             }
             if (nx && st == STEGO_OK) {
-                if (cudaMemcpyAsync(s.d_desc_x, s.h_desc_x, sizeof(stego_desc) * nx,
-                                    cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
+                if (nbx && cudaMemcpyAsync(s.d_desc_x, s.h_desc_x, sizeof(stego_desc) * nbx,
+                                           cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
                     st = STEGO_E_CUDA;
-                if (st == STEGO_OK)
-                    st = stego_extract_batched(s.d_desc_x, nx, s.d_res_x, 0, &cfg.tune_extract,
+                if (st == STEGO_OK && nbx)
+                    st = stego_extract_batched(s.d_desc_x, nbx, s.d_res_x, 0, &cfg.tune_extract,
                                                s.d_ws_x, s.ws_bytes, s.stream);
+                if (st == STEGO_OK && nx > nbx)
+                    st = launch_singles(s, false);
                 if (st == STEGO_OK &&
                     cudaMemcpyAsync(s.h_res_x, s.d_res_x, sizeof(stego_result) * nx,
                                     cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)

@@ -148,8 +148,13 @@ def test_budget_and_bad_requests(S):
                      cover_bytes=C, msg_bytes=C // 8, tag=102))            # too long a message
     recs.append(dict(op=S.OP_EMBED, flags=S.LAYOUT_PAPER2, cover=covers[2], stego=outs[2],
                      msg=msg, cover_bytes=C, msg_bytes=10, tag=103))       # no geometry
-    recs.append(dict(op=S.OP_EMBED, flags=S.BITS(2) | S.HEADER_BE32, cover=covers[2],
-                     stego=outs[2], msg=msg, cover_bytes=C, msg_bytes=10, tag=104))  # k = 2
+    spare = [torch.full((C,), 0x5A, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    recs.append(dict(op=S.OP_EMBED, flags=S.BITS(2) | S.PLANE_ONLY | S.HEADER_BE32,
+                     cover=covers[2], stego=spare[0], msg=msg, cover_bytes=C, msg_bytes=10,
+                     tag=104))  # one plane without a geometry: refused by the single-cover call
+    recs.append(dict(op=S.OP_EMBED, flags=S.BITS(3) | S.HEADER_BE32, cover=covers[2],
+                     stego=spare[1], msg=msg, cover_bytes=2048, msg_bytes=1000,
+                     tag=105))  # k = 3: 2048 bytes carry 764 message bytes, refused
     budget = 5 * C  # two embeds of 2C + 1000 fit, a third does not
     srv = S.Server(slots=3, max_batch=8, budget_bytes=budget)
     srv.submit(S.Server.requests(recs))
@@ -157,7 +162,7 @@ def test_budget_and_bad_requests(S):
     comps = _by_tag(srv.poll())
     st = srv.stats()
     srv.close()
-    assert sorted(comps) == list(range(6)) + [100, 101, 102, 103, 104]
+    assert sorted(comps) == list(range(6)) + [100, 101, 102, 103, 104, 105]
     for i in range(6):
         assert int(comps[i]["status"]) == 0
     assert int(comps[100]["status"]) == S.E_NOMEM
@@ -165,6 +170,8 @@ def test_budget_and_bad_requests(S):
     assert int(comps[102]["status"]) == S.E_CAPACITY
     assert int(comps[103]["status"]) == S.E_INVAL
     assert int(comps[104]["status"]) == S.E_INVAL
+    assert int(comps[105]["status"]) == S.E_CAPACITY
+    assert all(bool((t == 0x5A).all()) for t in spare)
     assert 0 < st["peak_in_flight_bytes"] <= budget
     assert st["outstanding"] == 0
     torch.cuda.synchronize()
@@ -238,3 +245,63 @@ def test_paper_layout_requests(S):
             assert np.array_equal(got[:N], w) and np.all(got[N:] == 0xEE), i
     assert all(int(comps[2 * i + 1]["status"]) == 0 and int(comps[2 * i + 1]["msg_bytes"]) == 100
                for i in range(40))
+
+
+def test_kbit_and_plane_requests(S):
+    """Stream-layout requests with k = 2..4 bits per byte and with one
+    carrying plane (k = 1, 2 on RGB covers), embed and extract, served in
+    the same batches as one-bit requests; every output and statistic equals
+    the oracle's."""
+    O = oracle.load()
+    rng = np.random.default_rng(44)
+    kinds = [(2, None), (3, None), (4, None), (1, (64, 33, 3, 1)), (2, (100, 7, 3, 0)),
+             (3, (16, 16, 4, 3))]
+    recs, want, keep = [], [], []
+    for i in range(48):
+        k, geom = kinds[i % len(kinds)]
+        n = geom[0] * geom[1] * geom[2] if geom else int(rng.integers(40, 20000))
+        cov = rng.integers(0, 256, n, dtype=np.uint8)
+        flags = S.BITS(k) | S.HEADER_BE32 | (S.PLANE_ONLY if geom else 0)
+        cap = S.stego_capacity(n, flags, geom=geom)
+        m = int(rng.integers(0, cap + 1))
+        msg = rng.integers(0, 256, m, dtype=np.uint8)
+        st, w = O.streamk_embed(cov, msg, k, header=True, geom=geom)
+        assert st == oracle.OK
+        geo = dict(width=geom[0], height=geom[1], channels=geom[2], plane=geom[3]) if geom else {}
+        c = torch.from_numpy(cov).cuda()
+        if i % 2 == 0:
+            mt = torch.from_numpy(msg).cuda()
+            o = torch.full((n,), 0x5A, dtype=torch.uint8, device="cuda")
+            recs.append(dict(op=S.OP_EMBED, flags=flags, cover=c, stego=o, msg=mt,
+                             cover_bytes=n, msg_bytes=m, **geo))
+            want.append(("embed", o, w, O.changed_bytes(cov, w), m))
+            keep += [c, mt, o]
+        else:
+            stg = torch.from_numpy(w).cuda()
+            o = torch.full((m + 3,), 0xEE, dtype=torch.uint8, device="cuda")
+            recs.append(dict(op=S.OP_EXTRACT, flags=flags, cover=stg, msg=o,
+                             cover_bytes=n, msg_bytes=m + 3, **geo))
+            want.append(("extract", o, msg, None, m))
+            keep += [stg, o]
+        # a one-bit request between them
+        cs = torch.from_numpy(rng.integers(0, 256, 4096, dtype=np.uint8)).cuda()
+        ms = torch.from_numpy(rng.integers(0, 256, 100, dtype=np.uint8)).cuda()
+        os_ = torch.empty_like(cs)
+        keep += [cs, ms, os_]
+        recs.append(dict(op=S.OP_EMBED, flags=S.HEADER_BE32, cover=cs, stego=os_, msg=ms,
+                         cover_bytes=4096, msg_bytes=100))
+    srv = S.Server(slots=3, max_batch=16, budget_bytes=1 << 32)
+    arrivals = synth.poisson_arrivals(100000.0, len(recs), 6)
+    comps = _by_tag(srv.run_open_loop(S.Server.requests(recs), arrivals, timeout_s=60))
+    srv.close()
+    for i, (kind, o, w, stats, m) in enumerate(want):
+        c = comps[2 * i]
+        assert int(c["status"]) == 0 and int(c["msg_bytes"]) == m, (i, c)
+        got = o.cpu().numpy()
+        if kind == "embed":
+            assert np.array_equal(got, w), i
+            assert (int(c["changed"]), int(c["sse"])) == stats, i
+        else:
+            assert np.array_equal(got[:m], w) and np.all(got[m:] == 0xEE), i
+    assert all(int(comps[2 * i + 1]["status"]) == 0 for i in range(48))
+    assert max(int(c["batch_size"]) for c in comps.values()) > 1
