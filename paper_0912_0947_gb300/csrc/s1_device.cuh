@@ -328,6 +328,17 @@ __device__ __forceinline__ void embed_shift_range(const EmbedView &a, uint32_t h
             }
             continue;
         }
+        if (jl < j_end && h + (j0 << 4) >= a.t_bytes) {
+            // the whole round past the carrying bytes: a copy, all loads
+            // first
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                c[u] = __ldcs(src + j0 + (uint64_t)u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                __stcs(dst + j0 + (uint64_t)u * blockDim.x, c[u]);
+            continue;
+        }
         // a round at an edge: one vector at a time, with the checks
 #pragma unroll 1
         for (int u = 0; u < V; ++u) {
@@ -402,6 +413,20 @@ __device__ __forceinline__ void embed_funnel_range(const EmbedView &a, uint32_t 
                     n += vec_changes(o, c);
                 __stcs(dst + j0 + (uint64_t)u * vstep, o);
             }
+            continue;
+        }
+        if (jl < j_end && j0 >= safe_lo && jl < safe_hi && h + (j0 << 4) >= a.t_bytes) {
+            // the whole round past the carrying bytes: a copy of joined
+            // vectors, all loads first
+            uint4 lo[V], hi[V];
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                lo[u] = __ldcs(A + j0 + (uint64_t)u * vstep);
+                hi[u] = __ldcs(A + j0 + (uint64_t)u * vstep + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                __stcs(dst + j0 + (uint64_t)u * vstep, funnel16<Q>(lo[u], hi[u], sel));
             continue;
         }
 #pragma unroll 1
