@@ -670,20 +670,20 @@ __global__ void __launch_bounds__(512) persist_extract(const stego_desc *descs, 
 // from 80 to 94 registers and persist_extract<4> from 39 to 64).  A tile is
 // per_tile aligned stego vectors (embed) or message byte pairs (extract);
 // the routines are the single-cover kernels' (same misalignment: vectors
-// after a scalar head; different misalignments: each stego vector joined
-// from the two aligned cover vectors around its bytes; extraction: aligned
-// stego vectors reduced to their LSBs, a pair's bits cut from two lanes'),
-// two vectors per thread and round for the embeds, four for the
-// extraction.
-constexpr int kMisV = 2, kMisXV = 4;
+// after a scalar head, two per thread and round; different misalignments:
+// each stego vector joined from the two aligned cover vectors around its
+// bytes, the second passed from the next lane, blocks of 4 x 32 vectors per
+// warp; extraction: aligned stego vectors reduced to their LSBs, a pair's
+// bits cut from two lanes', four per thread).
+constexpr int kMisV = 2, kMisFunnelV = 4, kMisXV = 4;
 
 template <int Q, bool STATS>
 __device__ __forceinline__ void mis_funnel(const s1::EmbedView &a, uint32_t h, uint32_t sel,
                                            uint64_t j0, uint64_t j1, unsigned long long &changed,
                                            unsigned long long &sse)
 {
-    s1::embed_funnel_range<Q, STATS, kMisV>(a, h, sel, j0 + threadIdx.x, j1,
-                                            (uint64_t)blockDim.x * kMisV, changed, sse);
+    s1::embed_funnel_warp<Q, STATS, kMisFunnelV>(a, h, sel, j0, j1, threadIdx.x >> 5,
+                                                 blockDim.x >> 5, changed, sse);
 }
 
 // One tile of a misaligned stream cover (the CTA's threads together).
@@ -752,14 +752,21 @@ __device__ __forceinline__ void mis_extract_tile(const stego_desc &D, const Desc
             s1::extract_one(x, x.len - 1);
 }
 
-// The misaligned stream tiles' own persistent kernels, so that a misaligned
-// batch keeps 32 warps per SM (inside the paper layout's 80-register kernel
-// it ran with 24: 4096 covers, embed 0.69 of the HBM peak there, 0.75 here).
-// The embed runs 512 threads per CTA, the extract 256 (a 64 KiB tile is four
-// rounds of its warps instead of two: 0.87 against 0.76 of the peak).
-constexpr int kMisEmbedThreads = 512, kMisExtractThreads = 256;
+// The misaligned stream tiles' own persistent kernels, with register
+// budgets of their own (inside the paper layout's kernel the embed ran at
+// 0.69 of the HBM peak on 4096 covers).  The embed runs three CTAs of 256
+// threads per SM at 80 registers: with one cover load per stego vector
+// (the funnel's second vector shuffled from the next lane) four vectors per
+// lane fit, 48 KiB of cover in flight per SM; on the 4096-cover batch at
+// offsets 1..15 that took the embed from 2.95 to 2.67 ms (0.83 to 0.92 of
+// the peak; the two-load form at two vectors: two CTAs of 512 threads at
+// 64 registers; the shuffled form at two vectors or at four in two CTAs of
+// 512 threads: 2.92-2.97 ms).  The extract runs 256 threads (a 64 KiB tile
+// is four rounds of its warps instead of two: 0.87 against 0.76 of the
+// peak).
+constexpr int kMisEmbedThreads = 256, kMisEmbedMinCtas = 3, kMisExtractThreads = 256;
 template <bool STATS>
-__global__ void __launch_bounds__(512) persist_mis_embed(const stego_desc *descs, uint32_t n,
+__global__ void __launch_bounds__(kMisEmbedThreads, kMisEmbedMinCtas) persist_mis_embed(const stego_desc *descs, uint32_t n,
                                                          stego_result *results, WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before

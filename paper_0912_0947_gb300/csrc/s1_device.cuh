@@ -234,6 +234,16 @@ __device__ __forceinline__ uint32_t stream_bits16_inner(const EmbedView &a, uint
     return (bits >> 8) | ((bits & 0xFFu) << 8);
 }
 
+// The 16 stream bits of a vector from the stream bytes b = S[q] | S[q+1] << 8
+// | S[q+2] << 16 (little-endian word) cut at bit s of S[q], as S[2v] |
+// S[2v+1] << 8 would give them for an aligned vector.
+__device__ __forceinline__ uint32_t bits16_from(uint32_t b, uint32_t s)
+{
+    const uint32_t w = __byte_perm(b, 0u, 0x4012u); // S[q] << 16 | S[q+1] << 8 | S[q+2]
+    const uint32_t bits = (w >> (8u - s)) & 0xFFFFu;
+    return (bits >> 8) | ((bits & 0xFFu) << 8);
+}
+
 // Cover vector c with its 16 stream bits p (as S[2v] | S[2v+1] << 8) ->
 // stego vector, all 16 bytes carrying.
 __device__ __forceinline__ uint4 spread16(const uint4 &c, uint32_t p)
@@ -366,89 +376,144 @@ __device__ __forceinline__ uint4 funnel16(const uint4 &lo, const uint4 &hi, uint
                       __byte_perm(w[Q + 2], w[Q + 3], sel), __byte_perm(w[Q + 3], w[Q + 4], sel));
 }
 
+// The aligned vector after lane l's lo[u] in a warp's block of 32*V
+// consecutive vectors (lane l + 1's lo[u]; for lane 31 lane 0's lo[u + 1], or
+// x, the vector after the block): one shuffle per word.  Lane 0's offer is
+// read only by lane 31.
+template <int V>
+__device__ __forceinline__ uint4 next_vec(const uint4 (&lo)[V], const uint4 &x, int u,
+                                          uint32_t lane)
+{
+    const uint4 give = lane == 0 ? (u + 1 < V ? lo[u + 1 < V ? u + 1 : u] : x) : lo[u];
+    const uint32_t src = (lane + 1u) & 31u;
+    return make_uint4(__shfl_sync(0xFFFFFFFFu, give.x, src), __shfl_sync(0xFFFFFFFFu, give.y, src),
+                      __shfl_sync(0xFFFFFFFFu, give.z, src), __shfl_sync(0xFFFFFFFFu, give.w, src));
+}
+
+// Stego vector j of embed_funnel_warp with every check: its cover bytes
+// from the two aligned cover vectors around them when both lie inside the
+// cover, else one by one; returns its changed bytes (0 without STATS).
+template <int Q, bool STATS>
+static __device__ __noinline__ uint32_t funnel_edge_vec(const EmbedView &a, uint32_t h,
+                                                        uint32_t sel, uint64_t j)
+{
+    const uint4 *A = reinterpret_cast<const uint4 *>((uintptr_t)(a.cover + h) & ~(uintptr_t)15u);
+    const uintptr_t lo_ok = (uintptr_t)a.cover, hi_ok = (uintptr_t)a.cover + a.n_bytes;
+    const uintptr_t b = (uintptr_t)(A + j);
+    const uint64_t k0 = h + (j << 4);
+    uint4 c;
+    if (b >= lo_ok && b + 32u <= hi_ok) {
+        const uint4 lo = __ldcs(A + j), hi = __ldcs(A + j + 1);
+        c = funnel16<Q>(lo, hi, sel);
+    } else {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            w[t >> 2] |= (uint32_t)a.cover[k0 + t] << (8 * (t & 3));
+        c = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    const uint32_t p = k0 < a.t_bytes ? stream_bits16(a, k0) : 0u;
+    uint32_t n = 0;
+    __stcs(reinterpret_cast<uint4 *>(a.stego + h) + j, embed_vec16_at<STATS>(a, k0, c, p, n));
+    return n;
+}
+
 // Cover and stego at different addresses mod 16 (out of place, n_bytes =
 // C): h = (-stego) mod 16 head bytes, then aligned stego vectors j at stego
-// + h + 16j (j < j_end).  The cover bytes of vector j, h + 16j .. h + 16j +
-// 15, start at byte d = (cover + h) mod 16 = 4Q + (sel's b) of the aligned
-// cover vector at or below them: they come from that vector and the next,
-// each loaded whole, joined by funnel16.  A vector whose two cover vectors
-// are not both inside the cover reads its 16 cover bytes one by one.  Head
-// and tail bytes are left to the caller.
-template <int Q, bool STATS, int V = 1>
-__device__ __forceinline__ void embed_funnel_range(const EmbedView &a, uint32_t h, uint32_t sel,
-                                                   uint64_t j_first, uint64_t j_end,
-                                                   uint64_t step, unsigned long long &changed,
-                                                   unsigned long long &sse)
+// + h + 16j (j_lo <= j < j_hi).  The cover bytes of vector j, h + 16j .. h +
+// 16j + 15, start at byte d = (cover + h) mod 16 = 4Q + (sel's b) of the
+// aligned cover vector A[j] at or below them: they are A[j]'s last 16 - d
+// bytes and A[j + 1]'s first d, joined by funnel16.
+//
+// Warp `warp` of `nwarps` takes rounds of 32*V consecutive stego vectors,
+// lane l vectors r + 32u + l.  Each lane loads only its own A[j]; A[j + 1] is
+// the next lane's, passed by one shuffle per word, and lane 31's is the
+// next block's first vector (lane 0 passes A[r + 32(u+1)], and one extra
+// vector A[r + 32V] per round): one cover load per stego vector, and 4V + 4
+// registers of cover data in flight where the two-load form needs 8V.
+// Rounds wholly inside the cover and the message (or wholly past the
+// carrying bytes: a copy) run without per-vector tests; a round at an edge
+// goes vector by vector, reading its 16 cover bytes one by one where A[j] or
+// A[j + 1] is not inside the cover.  Head and tail bytes are left to the
+// caller.
+template <int Q, bool STATS, int V>
+__device__ __forceinline__ void embed_funnel_warp(const EmbedView &a, uint32_t h, uint32_t sel,
+                                                  uint64_t j_lo, uint64_t j_hi, uint64_t warp,
+                                                  uint64_t nwarps, unsigned long long &changed,
+                                                  unsigned long long &sse)
 {
     const uintptr_t c0 = (uintptr_t)(a.cover + h);
     const uint4 *__restrict__ A = reinterpret_cast<const uint4 *>(c0 & ~(uintptr_t)15u);
     const uintptr_t lo_ok = (uintptr_t)a.cover, hi_ok = (uintptr_t)a.cover + a.n_bytes;
     uint4 *dst = reinterpret_cast<uint4 *>(a.stego + h);
+    const uint32_t lane = threadIdx.x & 31u;
     uint32_t n = 0;
     // stego vectors [safe_lo, safe_hi) have both cover vectors inside the cover
     const uint64_t safe_lo = (uintptr_t)A >= lo_ok ? 0u : 1u;
     const uint64_t nv = (hi_ok - (uintptr_t)A) >> 4;
     const uint64_t safe_hi = nv >= 1 ? nv - 1 : 0u;
-    const uint64_t vstep = V > 1 ? step / V : step; // the V vectors of a round
-    for (uint64_t j0 = j_first; j0 < j_end; j0 += step) {
-        const uint64_t jl = j0 + (uint64_t)(V - 1) * vstep;
-        if (jl < j_end && j0 >= safe_lo && jl < safe_hi &&
-            window_inner(a, h + (j0 << 4), h + (jl << 4))) {
-            // the whole round inside: no per-vector checks
-            uint4 lo[V], hi[V];
+    // cover byte h + 16j carries stream bit h + 16j: stream byte h/8 + 2j
+    // (message byte m0 + 2j), cut at bit h % 8
+    const uintptr_t m0 = (uintptr_t)a.msg + (h >> 3) - (a.header ? 4u : 0u);
+    const uint32_t bsh = h & 7u;
+    for (uint64_t r = j_lo + warp * 32u * V; r < j_hi; r += nwarps * 32u * V) {
+        const uint64_t re = r + 32u * V; // one past the round's last vector
+        const bool inside = re <= j_hi && r >= safe_lo && re <= safe_hi;
+        if (inside && window_inner(a, h + (r << 4), h + ((re - 1) << 4))) {
+            // the whole round inside the cover and the message
+            const uint4 *__restrict__ Ar = A + r + lane;
+            uint4 lo[V];
 #pragma unroll
-            for (int u = 0; u < V; ++u) {
-                lo[u] = __ldcs(A + j0 + (uint64_t)u * vstep);
-                hi[u] = __ldcs(A + j0 + (uint64_t)u * vstep + 1);
-            }
+            for (int u = 0; u < V; ++u)
+                lo[u] = __ldcs(Ar + 32u * u);
+            uint4 x = make_uint4(0u, 0u, 0u, 0u);
+            if (lane == 0)
+                x = __ldcs(Ar + 32u * V);
+            // stream bytes of vector j start at message byte m0 + 2j: the
+            // same offset within an aligned word for all V vectors of a lane
+            const uintptr_t pm = m0 + 2u * (r + lane);
+            const uint32_t *__restrict__ wp = reinterpret_cast<const uint32_t *>(pm & ~(uintptr_t)3u);
+            const uint32_t wsh = 8u * (uint32_t)(pm & 3u);
             uint32_t p[V];
 #pragma unroll
             for (int u = 0; u < V; ++u)
-                p[u] = stream_bits16_inner(a, h + ((j0 + (uint64_t)u * vstep) << 4));
+                p[u] = bits16_from(__funnelshift_r(__ldg(wp + 16u * u), __ldg(wp + 16u * u + 1), wsh),
+                                   bsh);
+            uint4 *Dr = dst + r + lane;
 #pragma unroll
             for (int u = 0; u < V; ++u) {
-                const uint4 c = funnel16<Q>(lo[u], hi[u], sel);
+                const uint4 c = funnel16<Q>(lo[u], next_vec<V>(lo, x, u, lane), sel);
                 const uint4 o = spread16(c, p[u]);
                 if (STATS)
                     n += vec_changes(o, c);
-                __stcs(dst + j0 + (uint64_t)u * vstep, o);
+                __stcs(Dr + 32u * u, o);
             }
             continue;
         }
-        if (jl < j_end && j0 >= safe_lo && jl < safe_hi && h + (j0 << 4) >= a.t_bytes) {
-            // the whole round past the carrying bytes: a copy of joined
-            // vectors, all loads first
-            uint4 lo[V], hi[V];
-#pragma unroll
-            for (int u = 0; u < V; ++u) {
-                lo[u] = __ldcs(A + j0 + (uint64_t)u * vstep);
-                hi[u] = __ldcs(A + j0 + (uint64_t)u * vstep + 1);
-            }
+        if (inside && h + (r << 4) >= a.t_bytes) {
+            // the whole round past the carrying bytes: a copy
+            const uint4 *__restrict__ Ar = A + r + lane;
+            uint4 lo[V];
 #pragma unroll
             for (int u = 0; u < V; ++u)
-                __stcs(dst + j0 + (uint64_t)u * vstep, funnel16<Q>(lo[u], hi[u], sel));
+                lo[u] = __ldcs(Ar + 32u * u);
+            uint4 x = make_uint4(0u, 0u, 0u, 0u);
+            if (lane == 0)
+                x = __ldcs(Ar + 32u * V);
+            uint4 *Dr = dst + r + lane;
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                __stcs(Dr + 32u * u, funnel16<Q>(lo[u], next_vec<V>(lo, x, u, lane), sel));
             continue;
         }
+        // a round at an edge: one vector at a time, with the checks, out of
+        // line (inlined, its registers doubled those of the batched kernel)
 #pragma unroll 1
         for (int u = 0; u < V; ++u) {
-        const uint64_t j = j0 + (uint64_t)u * vstep;
-        if (j >= j_end)
-            break;
-        const uintptr_t b = (uintptr_t)(A + j);
-        const uint64_t k0 = h + (j << 4);
-        uint4 c;
-        if (b >= lo_ok && b + 32u <= hi_ok) {
-            const uint4 lo = __ldcs(A + j), hi = __ldcs(A + j + 1);
-            c = funnel16<Q>(lo, hi, sel);
-        } else {
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int t = 0; t < 16; ++t)
-                w[t >> 2] |= (uint32_t)a.cover[k0 + t] << (8 * (t & 3));
-            c = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        const uint32_t p = k0 < a.t_bytes ? stream_bits16(a, k0) : 0u;
-        __stcs(dst + j, embed_vec16_at<STATS>(a, k0, c, p, n));
+            const uint64_t j = r + 32u * u + lane;
+            if (j >= j_hi)
+                break;
+            n += funnel_edge_vec<Q, STATS>(a, h, sel, j);
         }
     }
     if (STATS) {

@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(512) embed_shift(EmbedArgs e, uint32_t h)
 
 // Cover and stego at different addresses mod 16, out of place: aligned
 // stego vectors after h head bytes, each from two aligned cover vectors
-// (cover + h is 4Q + b bytes past a 16-byte boundary), V of them per thread
-// and round; block 0 does the head and the tail (fewer than 32 bytes).
+// (cover + h is 4Q + b bytes past a 16-byte boundary), the grid's warps
+// taking blocks of 32*V consecutive stego vectors; block 0 does the head and
+// the tail (fewer than 32 bytes).
 // Requires n_bytes >= h.
 template <int Q, int V, bool STATS>
 __global__ void __launch_bounds__(512) embed_funnel(EmbedArgs e, uint32_t h, uint32_t sel)
@@ -117,9 +118,9 @@ __global__ void __launch_bounds__(512) embed_funnel(EmbedArgs e, uint32_t h, uin
     unsigned long long changed = 0, sse = 0;
     write_res(e, STATS);
     const uint64_t nvb = (e.a.n_bytes - h) >> 4;
-    s1::embed_funnel_range<Q, STATS, V>(e.a, h, sel,
-                                        (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nvb,
-                                        (uint64_t)gridDim.x * blockDim.x * V, changed, sse);
+    s1::embed_funnel_warp<Q, STATS, V>(e.a, h, sel, 0, nvb,
+                                       ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                                       ((uint64_t)gridDim.x * blockDim.x) >> 5, changed, sse);
     if (blockIdx.x == 0)
         head_tail<STATS>(e.a, h, nvb, changed, sse);
     if (STATS)
@@ -217,11 +218,14 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // Vectors in flight per thread in the misaligned kernels, measured on the
 // 201 MB cover at full capacity (with the check-free interior rounds):
 // same misalignment embed 69.6 / 69.7 / 69.2 us for 1 / 2 / 4 (83-88 us
-// before those rounds); different misalignments 82.7 / 72.4-73.7 / 71.7-84.7
-// us; extraction 48.7 (vector pairs, one per thread) / 43-44 / 36.1-36.9 us
-// (LSB words shuffled between lanes).
+// before those rounds); different misalignments, both cover vectors loaded
+// per stego vector, 82.7 / 72.4-73.7 / 71.7-84.7 us, and with the second
+// vector shuffled from the next lane 71.7-74.5 us at 2 and 4 alike (4 kept:
+// the batched kernel shares the routine and gains there); extraction 48.7
+// (vector pairs, one per thread) / 43-44 / 36.1-36.9 us (LSB words shuffled
+// between lanes).
 constexpr int kShiftV = 2;
-constexpr int kFunnelV = 2;
+constexpr int kFunnelV = 4;
 constexpr int kExtractShiftV = 4;
 
 int clamp_vec(int v) { return (v == 1 || v == 2 || v == 8) ? v : 4; }
