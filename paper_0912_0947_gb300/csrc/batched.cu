@@ -761,13 +761,15 @@ __device__ __forceinline__ void mis_extract_tile(const stego_desc &D, const Desc
 // offsets 1..15 that took the embed from 2.95 to 2.67 ms (0.83 to 0.92 of
 // the peak; the two-load form at two vectors: two CTAs of 512 threads at
 // 64 registers; the shuffled form at two vectors or at four in two CTAs of
-// 512 threads: 2.92-2.97 ms).  The extract runs 256 threads (a 64 KiB tile
-// is four rounds of its warps instead of two: 0.87 against 0.76 of the
-// peak).
-constexpr int kMisEmbedThreads = 256, kMisEmbedMinCtas = 3, kMisExtractThreads = 256;
+// 512 threads: 2.92-2.97 ms).  The extract runs CTAs of 128 threads (48
+// registers, ten per SM), a 64 KiB tile being eight rounds of their warps:
+// on the same batch 0.84 ms with 256 threads, 0.75 ms with 128, as fast as
+// the aligned batch in the same launch shape (512 threads: 0.87 against
+// 0.76 of the peak with 256; eight vectors per lane: 0.75-0.77 ms).
+constexpr int kMisEmbedThreads = 256, kMisEmbedMinCtas = 3, kMisExtractThreads = 128;
 template <bool STATS>
-__global__ void __launch_bounds__(kMisEmbedThreads, kMisEmbedMinCtas) persist_mis_embed(const stego_desc *descs, uint32_t n,
-                                                         stego_result *results, WsView ws)
+__global__ void __launch_bounds__(kMisEmbedThreads, kMisEmbedMinCtas)
+    persist_mis_embed(const stego_desc *descs, uint32_t n, stego_result *results, WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
     allow_dependents();
@@ -785,8 +787,8 @@ __global__ void __launch_bounds__(kMisEmbedThreads, kMisEmbedMinCtas) persist_mi
         flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
 }
 
-__global__ void __launch_bounds__(256) persist_mis_extract(const stego_desc *descs, uint32_t n,
-                                                           WsView ws)
+__global__ void __launch_bounds__(kMisExtractThreads)
+    persist_mis_extract(const stego_desc *descs, uint32_t n, WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
     allow_dependents();
