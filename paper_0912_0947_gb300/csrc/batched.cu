@@ -73,6 +73,14 @@ constexpr uint32_t kFunnel = 8u;
 // paper-layout work kinds (0 = the one-bit stream layout)
 constexpr uint32_t kP2Units = 1u, kP2RowsCopy = 2u, kP2Rows = 3u, kP2Runs = 4u, kP2RowsX = 5u,
                    kP2UnitsInPlace = 6u;
+// Threads of the paper-layout persistent kernels' CTAs.  Unit and run tiles
+// hold a whole number of CTA rounds (tile_bytes rounded down), so that no
+// round runs with idle threads in the middle of a cover.
+constexpr uint32_t kP2Threads = 256u;
+__device__ __forceinline__ uint64_t whole_rounds(uint64_t per)
+{
+    return per >= kP2Threads ? per / kP2Threads * kP2Threads : per;
+}
 constexpr uint32_t kChunk = 4u; // tiles per claim
 
 // Workspace: head (64 B), aligned-stream, paper and misaligned-stream tile
@@ -204,7 +212,8 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
                 (uint64_t)D.geom.width / 16u * D.geom.height < (1ull << 31)) {
                 // one-pass units: grayscale, or RGB with any plane
                 const uint64_t units = (uint64_t)(D.geom.width / 16u) * D.geom.height;
-                const uint64_t per = tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u;
+                const uint64_t per =
+                    whole_rounds(tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u);
                 inf.mode = kP2Units;
                 inf.per_tile = (uint32_t)per;
                 tiles = (units + per - 1) / per;
@@ -213,7 +222,8 @@ __global__ void prep_embed(const stego_desc *descs, uint32_t n, stego_result *re
                        (uint64_t)D.geom.width / 16u * D.geom.height < (1ull << 31)) {
                 // in place: the units of the carrying rows, written back whole
                 const uint64_t units = (uint64_t)(D.geom.width / 16u) * v.R;
-                const uint64_t per = tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u;
+                const uint64_t per =
+                    whole_rounds(tile_bytes / (16u * ch) ? tile_bytes / (16u * ch) : 1u);
                 inf.mode = kP2UnitsInPlace;
                 inf.per_tile = (uint32_t)per;
                 tiles = (units + per - 1) / per;
@@ -341,9 +351,9 @@ __global__ void prep_extract(const stego_desc *descs, uint32_t n, stego_result *
                                              D.geom.channels, D.geom.plane, nullptr, nullptr, len);
             if (p2::unit_channels(D.geom.channels)) {
                 const uint64_t runs = (uint64_t)((v.Q + 15) / 16) * v.R;
-                const uint64_t per = tile_bytes / (64u * D.geom.channels)
-                                         ? tile_bytes / (64u * D.geom.channels)
-                                         : 1u;
+                const uint64_t per = whole_rounds(tile_bytes / (64u * D.geom.channels)
+                                                      ? tile_bytes / (64u * D.geom.channels)
+                                                      : 1u);
                 inf.mode = kP2Runs;
                 inf.per_tile = (uint32_t)per;
                 tiles = (runs + per - 1) / per;
@@ -804,7 +814,7 @@ __global__ void __launch_bounds__(kMisExtractThreads)
 // embed with statistics went from 1.47 to 1.32 ms and the extract from 0.54
 // to 0.48 ms, although the statistics variant spills (120 bytes).
 template <bool STATS>
-__global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *descs, uint32_t n,
+__global__ void __launch_bounds__(kP2Threads, 3) persist_p2_embed(const stego_desc *descs, uint32_t n,
                                                         stego_result *results, WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
@@ -823,7 +833,7 @@ __global__ void __launch_bounds__(256, 3) persist_p2_embed(const stego_desc *des
         flush_stats(changed, sse, stat_d < n ? results + stat_d : nullptr);
 }
 
-__global__ void __launch_bounds__(256, 3) persist_p2_extract(const stego_desc *descs, uint32_t n,
+__global__ void __launch_bounds__(kP2Threads, 3) persist_p2_extract(const stego_desc *descs, uint32_t n,
                                                           WsView ws)
 {
     grid_dependency_wait(); // launched dependent: nothing is touched before
@@ -930,7 +940,7 @@ int batched(const stego_desc *d_descs, uint32_t n, stego_result *d_results, uint
     if (e != cudaSuccess)
         return STEGO_E_CUDA;
     // paper-layout tiles (their count is on the device; an empty set exits at once)
-    const int p2_threads = 256;
+    const int p2_threads = (int)kP2Threads;
     const void *kp = EMBED ? (stats ? (const void *)persist_p2_embed<true>
                                     : (const void *)persist_p2_embed<false>)
                            : (const void *)persist_p2_extract;
