@@ -221,19 +221,6 @@ __device__ __forceinline__ uint32_t stream_bits16(const EmbedView &a, uint64_t k
     return (bits >> 8) | ((bits & 0xFFu) << 8);
 }
 
-// stream_bits16 where stream bytes q-3 .. q+7 (q = k0 / 8) are known to be
-// message bytes: no test.
-__device__ __forceinline__ uint32_t stream_bits16_inner(const EmbedView &a, uint64_t k0)
-{
-    const uint64_t q = k0 >> 3;
-    const uintptr_t pa = (uintptr_t)(a.msg + (q - (a.header ? 4u : 0u)));
-    const uint32_t *wp = reinterpret_cast<const uint32_t *>(pa & ~(uintptr_t)3u);
-    const uint32_t b = __funnelshift_r(__ldg(wp), __ldg(wp + 1), 8u * (uint32_t)(pa & 3u));
-    const uint32_t w = __byte_perm(b, 0u, 0x4012u);
-    const uint32_t bits = (w >> (8u - (uint32_t)(k0 & 7u))) & 0xFFFFu;
-    return (bits >> 8) | ((bits & 0xFFu) << 8);
-}
-
 // The 16 stream bits of a vector from the stream bytes b = S[q] | S[q+1] << 8
 // | S[q+2] << 16 (little-endian word) cut at bit s of S[q], as S[2v] |
 // S[2v+1] << 8 would give them for an aligned vector.
@@ -317,6 +304,10 @@ __device__ __forceinline__ void embed_shift_range(const EmbedView &a, uint32_t h
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(a.cover + h);
     uint4 *dst = reinterpret_cast<uint4 *>(a.stego + h);
     uint32_t n = 0;
+    // cover byte h + 16j carries stream bit h + 16j: stream byte h/8 + 2j
+    // (message byte m0 + 2j), cut at bit h % 8
+    const uintptr_t m0 = (uintptr_t)a.msg + (h >> 3) - (a.header ? 4u : 0u);
+    const uint32_t bsh = h & 7u;
     for (uint64_t j0 = j_first; j0 < j_end; j0 += step) {
         uint4 c[V];
         uint32_t p[V];
@@ -326,9 +317,17 @@ __device__ __forceinline__ void embed_shift_range(const EmbedView &a, uint32_t h
 #pragma unroll
             for (int u = 0; u < V; ++u)
                 c[u] = __ldcs(src + j0 + (uint64_t)u * blockDim.x);
+            // the V windows start 2 * blockDim.x message bytes apart, a
+            // multiple of 4: the same offset within an aligned word
+            const uintptr_t pm = m0 + 2u * j0;
+            const uint32_t *__restrict__ wp =
+                reinterpret_cast<const uint32_t *>(pm & ~(uintptr_t)3u);
+            const uint32_t wsh = 8u * (uint32_t)(pm & 3u);
 #pragma unroll
-            for (int u = 0; u < V; ++u)
-                p[u] = stream_bits16_inner(a, h + ((j0 + (uint64_t)u * blockDim.x) << 4));
+            for (int u = 0; u < V; ++u) {
+                const uint32_t *w = wp + (uint64_t)u * (blockDim.x >> 1);
+                p[u] = bits16_from(__funnelshift_r(__ldg(w), __ldg(w + 1), wsh), bsh);
+            }
 #pragma unroll
             for (int u = 0; u < V; ++u) {
                 const uint4 o = spread16(c[u], p[u]);

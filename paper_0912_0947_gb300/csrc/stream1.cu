@@ -218,13 +218,14 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // Vectors in flight per thread in the misaligned kernels, measured on the
 // 201 MB cover at full capacity (with the check-free interior rounds):
 // same misalignment embed 69.6 / 69.7 / 69.2 us for 1 / 2 / 4 (83-88 us
-// before those rounds); different misalignments, both cover vectors loaded
+// before those rounds), and with the message words' address computed once
+// per round 70.0-71.7 / 67.6-68.9 us for 2 / 4; different misalignments, both cover vectors loaded
 // per stego vector, 82.7 / 72.4-73.7 / 71.7-84.7 us, and with the second
 // vector shuffled from the next lane 71.7-74.5 us at 2 and 4 alike (4 kept:
 // the batched kernel shares the routine and gains there); extraction 48.7
 // (vector pairs, one per thread) / 43-44 / 36.1-36.9 us (LSB words shuffled
 // between lanes).
-constexpr int kShiftV = 2;
+constexpr int kShiftV = 4;
 constexpr int kFunnelV = 4;
 constexpr int kExtractShiftV = 4;
 
