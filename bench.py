@@ -1661,9 +1661,10 @@ def run_cpu_all_cores(cover, msg, budget_s=6.0):
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle as the reference arm: each step one embed + extract of a
-    bounded prefix of the workload, sized so that all steps take about a
-    minute."""
+    """The CPU oracle as the reference arm: each step one embed + extract of
+    the workload's whole cover, or of a prefix of it when the whole cover
+    would not let all steps finish in about a minute (`config.workload` and
+    `sample_bytes` say which)."""
     if rank != 0:
         return None
     import numpy as np
